@@ -1,0 +1,453 @@
+/*
+ * TEST INFRASTRUCTURE ONLY — not part of the product.
+ *
+ * A plain, slow, single-threaded FP64 CPU restatement of Lees-Edwards (LE)
+ * shear-flow molecular dynamics as described in Xu et al., "Implementation and
+ * Parallel Optimization of the Lees-Edwards Boundary Condition in ESPResSo++"
+ * (arXiv 2109.11083).  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may build, load or call this file.  It shares no code, header,
+ * table or helper with the CUDA library.
+ *
+ * Geometry (Sec. 2.1): flow along x, gradient along z, vorticity along y.  The
+ * box is [0,Lx) x [0,Ly) x [0,Lz).  The image box above the central box is
+ * displaced along x by dX(t) = gamma_dot * Lz * t (Fig. 1: 2*delta), reduced
+ * modulo Lx (Eq. 4).
+ *
+ * Readings of the paper that this file takes (each is listed with its reason
+ * in the design notes of the repository):
+ *   - leaving through the top: z -= Lz, x -= dX, vx -= gamma_dot*Lz; leaving
+ *     through the bottom: the mirror image (Eq. 4 with the sign of Fig. 1).
+ *   - friction acts on the half-step velocity; the random force is uniform
+ *     with variance 2*xi*kT*m/dt per component (the sqrt(24...)*U(-1/2,1/2)
+ *     pattern of Eq. 7).
+ *   - the random numbers come from Philox4x64-10 (Salmon et al., SC'11),
+ *     key = (seed, system), counter = (step, particle id, 0, 0).
+ *   - stress is the xz component of Eq. 15 (the text names xy, but with flow
+ *     along x and gradient along z the shear component is xz).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    double L[3];          /* box edges Lx, Ly, Lz */
+    double shear_rate;    /* gamma_dot, Eq. 1 */
+    double rc;            /* LJ cut-off radius (strict: r < rc) */
+    double eps, sigma;    /* LJ parameters, Eq. 9 */
+    int    lj_shift;      /* 1: energy shift of Eq. 10 (forces unchanged) */
+    double fene_k, fene_R0; /* FENE, Eq. 11 */
+    double mass, kT, xi, dt;
+    int    thermostat;    /* 0: none, 1: Langevin on peculiar velocity (Eq. 5) */
+    uint64_t seed, system;
+    int    nbins;         /* velocity-profile bins along z */
+} ora_params;
+
+enum { ORA_OK = 0, ORA_BOND_BROKEN = 1, ORA_BOX_TOO_SMALL = 2, ORA_NONFINITE = 3 };
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 4 / Fig. 1: x-offset of the image box above the central one at step n,
+ * computed from the integer step (never accumulated). */
+double ora_dX(const ora_params *p, int64_t n)
+{
+    double t = (double)n * p->dt;
+    double d = fmod(p->shear_rate * p->L[2] * t, p->L[0]);
+    if (d < 0.0) d += p->L[0];
+    return d;
+}
+
+/* Eq. 1: streaming velocity of the linear shear profile. */
+double ora_vs(const ora_params *p, double z)
+{
+    return p->shear_rate * (z - 0.5 * p->L[2]);
+}
+
+/* LE minimum image of r_i - r_j with image offset dX: the image across the
+ * top/bottom face is displaced along x by dX (Fig. 1); x and y are periodic. */
+void ora_min_image(const ora_params *p, double dX, const double *ri,
+                   const double *rj, double *d)
+{
+    double dx = ri[0] - rj[0], dy = ri[1] - rj[1], dz = ri[2] - rj[2];
+    if (dz > 0.5 * p->L[2]) {
+        dz -= p->L[2];
+        dx -= dX;
+    } else if (dz < -0.5 * p->L[2]) {
+        dz += p->L[2];
+        dx += dX;
+    }
+    dx -= p->L[0] * nearbyint(dx / p->L[0]);
+    dy -= p->L[1] * nearbyint(dy / p->L[1]);
+    d[0] = dx; d[1] = dy; d[2] = dz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+ * multiply-xor bijection with a Weyl-sequence key schedule. */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 prod = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(prod >> 64);
+    *lo = (uint64_t)prod;
+}
+
+void ora_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ULL, c0, &hi0, &lo0);
+        mulhilo64(0xCA5A826395121157ULL, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Three uniforms on [-1/2, 1/2) for particle `gid` at step `n`: the top 53
+ * bits of the first three Philox words, scaled by 2^-53. */
+void ora_noise(const ora_params *p, int64_t n, int64_t gid, double u[3])
+{
+    uint64_t ctr[4] = {(uint64_t)n, (uint64_t)gid, 0, 0};
+    uint64_t key[2] = {p->seed, p->system};
+    uint64_t out[4];
+    ora_philox4x64(ctr, key, out);
+    for (int k = 0; k < 3; ++k)
+        u[k] = (double)(out[k] >> 11) * 0x1.0p-53 - 0.5;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pair terms.  Eq. 9 (LJ) and Eq. 10 (shifted LJ): the force is the negative
+ * gradient of Eq. 9 for r < rc; the shift changes only the energy.  Returns
+ * f/r so that F_i = (f/r) * d. */
+static double lj_f_over_r(const ora_params *p, double r2, double *energy)
+{
+    double s2 = p->sigma * p->sigma / r2;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    double e = 4.0 * p->eps * (s12 - s6);
+    if (p->lj_shift) {
+        double c2 = p->sigma * p->sigma / (p->rc * p->rc);
+        double c6 = c2 * c2 * c2;
+        e -= 4.0 * p->eps * (c6 * c6 - c6);
+    }
+    *energy = e;
+    return 24.0 * p->eps * (2.0 * s12 - s6) / r2;
+}
+
+/* Eq. 11 (FENE): V = -1/2 k R0^2 ln(1 - (r/R0)^2) for r < R0, infinite
+ * otherwise.  Returns f/r = -k / (1 - (r/R0)^2), or sets *broken. */
+static double fene_f_over_r(const ora_params *p, double r2, double *energy, int *broken)
+{
+    double R02 = p->fene_R0 * p->fene_R0;
+    double x = 1.0 - r2 / R02;
+    if (!(x > 0.0)) {
+        *broken = 1;
+        *energy = INFINITY;
+        return 0.0;
+    }
+    *energy = -0.5 * p->fene_k * R02 * log(x);
+    return -p->fene_k / x;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Candidate-pair enumeration.  mode 0: every pair (i, j != i).  mode 1: a
+ * cell grid of edge >= rc (at least 3 cells per dimension, otherwise mode 0
+ * is used).  A neighbour row in y and z is scanned over the three adjacent x
+ * cells, except across the top/bottom face where the image row is displaced
+ * by dX: there the whole x row is scanned.  The candidates are a superset of
+ * the pairs within rc; each is then tested with the LE minimum image. */
+typedef struct {
+    int nc[3];
+    double lc[3];
+    int *head, *next;
+} cell_grid;
+
+static int grid_build(const ora_params *p, int64_t n, const double *pos, cell_grid *g)
+{
+    for (int a = 0; a < 3; ++a) {
+        g->nc[a] = (int)floor(p->L[a] / p->rc);
+        if (g->nc[a] < 3) return 0;
+        g->lc[a] = p->L[a] / g->nc[a];
+    }
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    g->head = (int *)malloc(sizeof(int) * ncell);
+    g->next = (int *)malloc(sizeof(int) * n);
+    for (int64_t c = 0; c < ncell; ++c) g->head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int)floor(pos[3 * i + a] / g->lc[a]);
+            if (c[a] < 0) c[a] = 0;
+            if (c[a] >= g->nc[a]) c[a] = g->nc[a] - 1;
+        }
+        int64_t cid = ((int64_t)c[2] * g->nc[1] + c[1]) * g->nc[0] + c[0];
+        g->next[i] = g->head[cid];
+        g->head[cid] = (int)i;
+    }
+    return 1;
+}
+
+static void grid_free(cell_grid *g)
+{
+    free(g->head);
+    free(g->next);
+}
+
+/* Calls visit(i, j) for every candidate j of particle i (j != i). */
+typedef void (*visit_fn)(void *ctx, int64_t i, int64_t j);
+
+static void for_candidates(const ora_params *p, int64_t n, const double *pos,
+                           int use_cells, void *ctx, visit_fn visit)
+{
+    cell_grid g;
+    if (!use_cells || !grid_build(p, n, pos, &g)) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j)
+                if (j != i) visit(ctx, i, j);
+        return;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int)floor(pos[3 * i + a] / g.lc[a]);
+            if (c[a] < 0) c[a] = 0;
+            if (c[a] >= g.nc[a]) c[a] = g.nc[a] - 1;
+        }
+        for (int dz = -1; dz <= 1; ++dz) {
+            int cz = c[2] + dz;
+            int across = (cz < 0 || cz >= g.nc[2]);
+            cz = (cz + g.nc[2]) % g.nc[2];
+            for (int dy = -1; dy <= 1; ++dy) {
+                int cy = (c[1] + dy + g.nc[1]) % g.nc[1];
+                int x0 = across ? 0 : c[0] - 1;
+                int x1 = across ? g.nc[0] - 1 : c[0] + 1;
+                for (int xx = x0; xx <= x1; ++xx) {
+                    int cx = (xx + g.nc[0]) % g.nc[0];
+                    int64_t cid = ((int64_t)cz * g.nc[1] + cy) * g.nc[0] + cx;
+                    for (int j = g.head[cid]; j >= 0; j = g.next[j])
+                        if (j != i) visit(ctx, i, j);
+                }
+            }
+        }
+    }
+    grid_free(&g);
+}
+
+typedef struct {
+    const ora_params *p;
+    double dX;
+    const double *pos;
+    double *F;
+    double W[9];
+    double epot;
+} pair_ctx;
+
+static void pair_visit(void *vctx, int64_t i, int64_t j)
+{
+    pair_ctx *c = (pair_ctx *)vctx;
+    double d[3];
+    ora_min_image(c->p, c->dX, c->pos + 3 * i, c->pos + 3 * j, d);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < c->p->rc * c->p->rc)) return;
+    double e;
+    double fr = lj_f_over_r(c->p, r2, &e);
+    for (int a = 0; a < 3; ++a) c->F[3 * i + a] += fr * d[a];
+    if (i < j) {  /* each unordered pair once in the energy and the virial */
+        c->epot += e;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) c->W[3 * a + b] += d[a] * fr * d[b];
+    }
+}
+
+/* Conservative forces at image offset dX: LJ over all pairs within rc plus
+ * FENE over the bond list.  W receives sum_{i<j} r_ij (x) F_ij (the virial
+ * part of Eq. 15), epot the potential energy (Eq. 13 without the angle term).
+ * Returns ORA_BOND_BROKEN if any bond reaches R0 (Eq. 11: +infinity). */
+int ora_forces(const ora_params *p, double dX, int64_t n, const double *pos,
+               int64_t nbond, const int32_t *bonds, int use_cells,
+               double *F, double *W, double *epot)
+{
+    pair_ctx c;
+    c.p = p; c.dX = dX; c.pos = pos; c.F = F; c.epot = 0.0;
+    memset(c.W, 0, sizeof c.W);
+    memset(F, 0, sizeof(double) * 3 * n);
+    if (p->eps != 0.0) for_candidates(p, n, pos, use_cells, &c, pair_visit);
+    int broken = 0;
+    for (int64_t b = 0; b < nbond; ++b) {
+        int64_t i = bonds[2 * b], j = bonds[2 * b + 1];
+        double d[3];
+        ora_min_image(p, dX, pos + 3 * i, pos + 3 * j, d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double e;
+        double fr = fene_f_over_r(p, r2, &e, &broken);
+        for (int a = 0; a < 3; ++a) {
+            F[3 * i + a] += fr * d[a];
+            F[3 * j + a] -= fr * d[a];
+        }
+        c.epot += e;
+        for (int a = 0; a < 3; ++a)
+            for (int q = 0; q < 3; ++q) c.W[3 * a + q] += d[a] * fr * d[q];
+    }
+    if (W) memcpy(W, c.W, sizeof c.W);
+    if (epot) *epot = c.epot;
+    return broken ? ORA_BOND_BROKEN : ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 5: total force = conservative - xi*m*(v - v_s(z) e_x) + random, the
+ * friction acting on the peculiar velocity.  v is the half-step velocity. */
+static void thermostat_force(const ora_params *p, int64_t step, int64_t n,
+                             const double *pos, const double *vel,
+                             const double *Fc, double *Ftot)
+{
+    double amp = sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) Ftot[3 * i + a] = Fc[3 * i + a];
+        if (p->thermostat != 1) continue;
+        double u[3];
+        ora_noise(p, step, i, u);
+        double vpec[3] = {vel[3 * i] - ora_vs(p, pos[3 * i + 2]), vel[3 * i + 1],
+                          vel[3 * i + 2]};
+        for (int a = 0; a < 3; ++a)
+            Ftot[3 * i + a] += -p->xi * p->mass * vpec[a] + amp * u[a];
+    }
+}
+
+/* Forces at step n for the state (pos, vel): fills Fc and Ftot.  Used to
+ * start a run (with the initial velocity standing in for the half-step one). */
+int ora_init_forces(const ora_params *p, int64_t step, int64_t n, const double *pos,
+                    const double *vel, int64_t nbond, const int32_t *bonds,
+                    int use_cells, double *Fc, double *Ftot, double *W, double *epot)
+{
+    int st = ora_forces(p, ora_dX(p, step), n, pos, nbond, bonds, use_cells, Fc, W, epot);
+    thermostat_force(p, step, n, pos, vel, Fc, Ftot);
+    return st;
+}
+
+/* Running samples (Eqs. 14-15 and the z-profiles of Sec. 3.1). */
+typedef struct {
+    int64_t nsamples;
+    double sxz_sum;          /* sum over samples of sigma_xz */
+    double stress[9];        /* last instantaneous tensor, Eq. 15 */
+    double tpec;             /* last peculiar temperature (3N-3 dof) */
+    double epot;             /* last potential energy */
+    double *vx_sum;          /* nbins: sum of lab-frame vx */
+    int64_t *count;          /* nbins */
+} ora_samples;
+
+static void sample(const ora_params *p, int64_t n, const double *pos,
+                   const double *vel, const double *W, double epot, ora_samples *s)
+{
+    double V = p->L[0] * p->L[1] * p->L[2];
+    double K[9] = {0};
+    double ke = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double u[3] = {vel[3 * i] - ora_vs(p, pos[3 * i + 2]), vel[3 * i + 1],
+                       vel[3 * i + 2]};
+        for (int a = 0; a < 3; ++a) {
+            ke += p->mass * u[a] * u[a];
+            for (int b = 0; b < 3; ++b) K[3 * a + b] += p->mass * u[a] * u[b];
+        }
+        if (s->vx_sum && p->nbins > 0) {
+            int bin = (int)floor(pos[3 * i + 2] / p->L[2] * p->nbins);
+            if (bin < 0) bin = 0;
+            if (bin >= p->nbins) bin = p->nbins - 1;
+            s->vx_sum[bin] += vel[3 * i];
+            s->count[bin] += 1;
+        }
+    }
+    for (int a = 0; a < 9; ++a) s->stress[a] = -(K[a] + W[a]) / V;
+    s->sxz_sum += s->stress[2];
+    s->nsamples += 1;
+    s->tpec = n > 1 ? ke / (3.0 * n - 3.0) : 0.0;
+    s->epot = epot;
+}
+
+/* One velocity-Verlet step n -> n+1 under LE (the order every implementation
+ * in this repository follows):
+ *   1. v += dt/(2m) Ftot(n)
+ *   2. r += dt v
+ *   3. dX(n+1) from the integer step
+ *   4. LE wrap through the top/bottom face with the velocity jump; x, y periodic
+ *   5. Fc(n+1): LJ + FENE with the LE minimum image at dX(n+1)
+ *   6. Ftot(n+1) = Fc - xi m (v - v_s(z) e_x) + random        (Eq. 5)
+ *   7. v += dt/(2m) Ftot(n+1)
+ *   8. samples (Eq. 15 stress, z-profile of vx, peculiar temperature)
+ * zimg (optional) counts each particle's net crossings through the top face. */
+int ora_run(const ora_params *p, int64_t *step, int64_t nsteps, int64_t n,
+            double *pos, double *vel, double *Fc, double *Ftot,
+            int64_t nbond, const int32_t *bonds, int use_cells,
+            int32_t *zimg, int sample_every, ora_samples *s)
+{
+    const double Lx = p->L[0], Ly = p->L[1], Lz = p->L[2];
+    const double half = p->dt / (2.0 * p->mass);
+    double W[9], epot;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] += half * Ftot[q];
+        for (int64_t q = 0; q < 3 * n; ++q) pos[q] += p->dt * vel[q];
+        int64_t next = *step + 1;
+        double dX = ora_dX(p, next);
+        for (int64_t i = 0; i < n; ++i) {
+            double *r = pos + 3 * i, *v = vel + 3 * i;
+            if (r[2] >= Lz) {
+                r[2] -= Lz;
+                r[0] -= dX;
+                v[0] -= p->shear_rate * Lz;
+                if (zimg) zimg[i] += 1;
+            } else if (r[2] < 0.0) {
+                double zz = r[2] + Lz;
+                if (zz < Lz) {
+                    r[2] = zz;
+                    r[0] += dX;
+                    v[0] += p->shear_rate * Lz;
+                    if (zimg) zimg[i] -= 1;
+                } else {
+                    /* z within rounding of 0 from below: the particle sits on
+                     * the bottom face, where no image shift is needed */
+                    r[2] = 0.0;
+                }
+            }
+            r[0] -= Lx * floor(r[0] / Lx);
+            r[1] -= Ly * floor(r[1] / Ly);
+            /* floor-based wrapping can round up to exactly L for tiny
+             * negative inputs; fold that back into [0, L) */
+            if (r[0] >= Lx) r[0] -= Lx;
+            if (r[1] >= Ly) r[1] -= Ly;
+        }
+        int st = ora_forces(p, dX, n, pos, nbond, bonds, use_cells, Fc, W, &epot);
+        if (st != ORA_OK) return st;
+        thermostat_force(p, next, n, pos, vel, Fc, Ftot);
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] += half * Ftot[q];
+        *step = next;
+        for (int64_t q = 0; q < 3 * n; ++q)
+            if (!isfinite(pos[q]) || !isfinite(vel[q])) return ORA_NONFINITE;
+        if (s && sample_every > 0 && (next % sample_every) == 0)
+            sample(p, n, pos, vel, W, epot, s);
+    }
+    return ORA_OK;
+}
+
+/* Instantaneous Eq. 15 tensor, peculiar temperature and potential energy of
+ * a state, without advancing it. */
+int ora_observe(const ora_params *p, int64_t step, int64_t n, const double *pos,
+                const double *vel, int64_t nbond, const int32_t *bonds,
+                int use_cells, double *stress9, double *tpec, double *epot)
+{
+    double *F = (double *)malloc(sizeof(double) * 3 * n);
+    double W[9], e;
+    int st = ora_forces(p, ora_dX(p, step), n, pos, nbond, bonds, use_cells, F, W, &e);
+    free(F);
+    ora_samples s;
+    memset(&s, 0, sizeof s);
+    sample(p, n, pos, vel, W, e, &s);
+    memcpy(stress9, s.stress, sizeof s.stress);
+    *tpec = s.tpec;
+    *epot = e;
+    return st;
+}
