@@ -1,0 +1,193 @@
+/*
+ * le.h — C ABI of the GB300 (sm_103a) Lees-Edwards shear-flow MD library.
+ *
+ * The method is Lees-Edwards (LE) sheared periodic boundaries for short-range
+ * molecular dynamics, after Xu et al., "Implementation and Parallel
+ * Optimization of the Lees-Edwards Boundary Condition in ESPResSo++"
+ * (arXiv 2109.11083).  One simulation handle holds one sheared box resident
+ * in GPU memory; every step of the method runs in this library's CUDA kernels.
+ *
+ * Geometry and conventions (Sec. 2.1 of the paper):
+ *   - flow along x, velocity gradient along z, vorticity along y;
+ *   - box [0,Lx) x [0,Ly) x [0,Lz); streaming profile v_s(z) =
+ *     shear_rate * (z - Lz/2) (Eq. 1);
+ *   - the image box above is displaced along x by
+ *     dX(t) = (shear_rate * Lz * t) mod Lx (Eq. 4, Fig. 1), with t = n * dt
+ *     taken from the integer step n;
+ *   - a particle leaving through the top face re-enters at the bottom with
+ *     x -= dX and vx -= shear_rate * Lz; through the bottom face the mirror
+ *     image (Eq. 4 with the sign of Fig. 1);
+ *   - reduced LJ units (Sec. 2.4): positions in sigma, energies in eps.
+ *
+ * Memory and threads: every pointer argument is a HOST pointer owned by the
+ * caller; the library copies inputs in and writes outputs into the caller's
+ * buffers (pinned buffers make the copies faster).  The library owns all of
+ * its device memory.  A handle must be used by one host thread at a time.
+ * Particle arrays are in the caller's order (particle id = row index) even
+ * though the library keeps particles sorted by cell internally.
+ *
+ * Errors: every call returns an le_status and never aborts.  le_last_error()
+ * describes the last failure on a handle.  When le_step fails with
+ * LE_ERR_BOND_BROKEN, LE_ERR_NONFINITE or LE_ERR_CAPACITY the state is rolled
+ * back to what it was when that le_step call began.
+ */
+#ifndef LE_H
+#define LE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LE_API __attribute__((visibility("default")))
+#else
+#define LE_API
+#endif
+
+typedef struct le_sim le_sim; /* opaque, library-owned */
+
+typedef enum le_status {
+    LE_OK = 0,
+    LE_ERR_INVALID_ARG = 1,   /* a null pointer, a size out of range, ... */
+    LE_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in le_last_error) */
+    LE_ERR_OOM = 3,           /* device memory could not be allocated */
+    LE_ERR_BOX_TOO_SMALL = 4, /* rc + skin must be below half of every box edge */
+    LE_ERR_BOND_BROKEN = 5,   /* a FENE bond reached R0 (Eq. 11: infinite energy) */
+    LE_ERR_NONFINITE = 6,     /* a force or velocity became NaN or infinite */
+    LE_ERR_CAPACITY = 7,      /* the neighbour list overflowed and could not grow */
+    LE_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
+    LE_ERR_STATE = 9          /* call order: e.g. le_step before le_set_particles */
+} le_status;
+
+typedef enum le_precision {
+    LE_FP64 = 0,              /* every quantity in FP64 */
+    LE_FP32 = 1               /* FP32 pair forces and velocities; positions kept
+                                 to FP64-class precision (see le_create) */
+} le_precision;
+
+typedef enum le_thermostat {
+    LE_THERMO_NONE = 0,
+    LE_THERMO_PECULIAR = 1    /* Langevin on the peculiar velocity v - v_s(z) e_x (Eq. 5) */
+} le_thermostat;
+
+typedef struct le_params {
+    double eps, sigma;        /* LJ parameters (Eq. 9) */
+    double mass;              /* particle mass m */
+    double kT;                /* target temperature k_B T */
+    double xi;                /* Langevin friction rate (Eq. 5): F = -xi m (v - v_s) + random */
+    double dt;                /* time step */
+    int    lj_shift;          /* 1: energy shift of Eq. 10 (does not change forces) */
+    int    thermostat;        /* le_thermostat */
+    double fene_k, fene_R0;   /* FENE bond (Eq. 11); used only when bonds are set */
+    int    precision;         /* le_precision */
+    uint64_t seed;            /* random-force stream: Philox4x64-10 with key (seed, system_id) */
+    uint64_t system_id;       /*   and counter (step, particle id, 0, 0)                       */
+    int    sample_every;      /* >0: accumulate stress and profile every this many steps */
+    int    profile_bins;      /* number of z bins of the velocity profile (1..1024) */
+} le_params;
+
+/* Fills *p with defaults: eps = sigma = mass = kT = xi = 1, dt = 0.005,
+ * lj_shift = 1, thermostat = LE_THERMO_PECULIAR, fene_k = 30, fene_R0 = 1.5,
+ * precision = LE_FP64, seed = 0, system_id = 0, sample_every = 1,
+ * profile_bins = 20. */
+LE_API void le_default_params(le_params *p);
+
+/* Creates a handle for the box [0,box[0]) x [0,box[1]) x [0,box[2]) sheared at
+ * shear_rate (Eq. 1), with LJ cut-off rc (strict r < rc) and Verlet skin
+ * `skin`.  The cell grid has edge >= rc + skin.  cuda_stream is a cudaStream_t
+ * (may be NULL for the legacy default stream); all device work of the handle
+ * is ordered on it.  In LE_FP32 mode positions are stored as an FP64 cell
+ * reference plus an FP32 (hi, lo) pair for the displacement from it, which
+ * keeps ~48 significant bits near the reference.
+ * Errors: LE_ERR_INVALID_ARG (null out/params, non-positive box, rc, dt or
+ * mass, negative skin, bins out of range), LE_ERR_BOX_TOO_SMALL
+ * (rc + skin >= half of an edge), LE_ERR_CUDA. */
+LE_API le_status le_create(const double box[3], double shear_rate, double rc, double skin,
+                           const le_params *p, void *cuda_stream, le_sim **out);
+
+/* Bonds for the FENE potential (Eq. 11): nb pairs of particle ids (nb x 2,
+ * row-major).  At most 8 bonds per particle.  Call before le_set_particles;
+ * calling it afterwards re-initialises the forces from the current state.
+ * Errors: LE_ERR_INVALID_ARG (id out of range once particles are set, a
+ * self-bond, more than 8 bonds on a particle). */
+LE_API le_status le_set_bonds(le_sim *s, int64_t nb, const int32_t *pairs);
+
+/* Loads n particles: pos (n x 3, row-major, any real coordinates; they are
+ * wrapped into the box as images at step 0, where dX = 0) and lab-frame vel
+ * (n x 3).  Resets the step counter to 0, the samples and the counters, builds
+ * the cell/Verlet lists and computes the initial total force.  1 <= n <= 2^25.
+ * Errors: LE_ERR_INVALID_ARG, LE_ERR_OOM, LE_ERR_BOND_BROKEN, LE_ERR_CUDA. */
+LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const double *vel);
+
+/* Advances nsteps >= 0 velocity-Verlet steps (kick, drift, LE wrap and
+ * velocity jump, rebuild when the skin-displacement + image-shift trigger
+ * fires, LJ/FENE forces under the LE minimum image, Langevin on the peculiar
+ * velocity, kick, samples).  Returns when the work has finished. */
+LE_API le_status le_step(le_sim *s, int64_t nsteps);
+
+/* Conservative forces (LJ + FENE) of the current step, n x 3 row-major. */
+LE_API le_status le_forces(le_sim *s, double *out);
+
+/* Current positions wrapped into the box (LE image at the current dX) and
+ * the matching lab-frame velocities, n x 3 each; either pointer may be NULL. */
+LE_API le_status le_positions(le_sim *s, double *pos, double *vel);
+
+/* out9: instantaneous Eq. 15 stress tensor of the current state, row-major
+ * (sigma = -(1/V)[sum m (v - v_s)(v - v_s) + sum_{i<j} r_ij F_ij]);
+ * xz_avg: mean of sigma_xz over the samples taken since the last reset;
+ * nsamples: how many.  Any pointer may be NULL.  Viscosity (Eq. 14) is
+ * xz_avg / shear_rate. */
+LE_API le_status le_stress(le_sim *s, double out9[9], double *xz_avg, int64_t *nsamples);
+
+/* Mean lab-frame vx in each of the nbins z-bins over the samples since the
+ * last reset (NaN for an empty bin), and the particle counts per bin.
+ * nbins must equal params.profile_bins. */
+LE_API le_status le_velocity_profile(le_sim *s, int nbins, double *vx_mean, int64_t *counts);
+
+/* Mean peculiar temperature (3N - 3 degrees of freedom) over the samples. */
+LE_API le_status le_temperature(le_sim *s, double *tpec_avg);
+
+/* Clears the running samples (stress, profile, temperature). */
+LE_API le_status le_reset_samples(le_sim *s);
+
+typedef struct le_counters {
+    int64_t step;             /* current integer step n */
+    int64_t particles;
+    int64_t rebuilds;         /* list rebuilds since le_set_particles */
+    int64_t image_rebuilds;   /* rebuilds the displacement alone would not have needed */
+    int64_t list_capacity;    /* neighbour slots per particle */
+    int64_t list_max;         /* largest neighbour count seen at a rebuild */
+    int64_t cells[3];         /* cell grid */
+    double  dX;               /* current image offset */
+} le_counters;
+
+LE_API le_status le_get_counters(le_sim *s, le_counters *out);
+
+/* Checkpoint: an opaque copy of the whole dynamical state in the library's
+ * internal (cell-sorted) layout: positions, velocities, forces, the integer
+ * step, the last list-build record and the running samples.  With
+ * buf == NULL, *bytes receives the size needed.  le_set_state accepts a blob
+ * from a handle with the same box, parameters and particle count; stepping
+ * after it reproduces the uninterrupted run bit for bit (the random force is
+ * a pure function of seed, system id, step and particle id). */
+LE_API le_status le_get_state(le_sim *s, void *buf, size_t *bytes);
+LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes);
+
+/* Runs nsteps like le_step, as ONE launch of a graph captured for exactly
+ * that many steps, with CUDA events around every launch of the pair-force
+ * kernel and of the integrate kernel.  Returns the summed device time of each
+ * (milliseconds) and the whole graph's device time.  Meant for measurement. */
+LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms,
+                                  double *integrate_ms, double *total_ms);
+
+LE_API le_status le_destroy(le_sim *s);
+LE_API const char *le_last_error(const le_sim *s);
+LE_API const char *le_status_string(le_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LE_H */

@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
                    check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -105,6 +105,9 @@ def lib():
             L.ora_run.argtypes = [C.POINTER(Params), C.POINTER(C.c_int64), C.c_int64,
                                   C.c_int64, _D, _D, _D, _D, C.c_int64, _I32, C.c_int,
                                   _I32, C.c_int, C.POINTER(Samples)]
+            L.ora_forces_on.restype = None
+            L.ora_forces_on.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
+                                        C.c_int64, C.POINTER(C.c_int64), _D]
             L.ora_observe.restype = C.c_int
             L.ora_observe.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, _D, _D,
                                       C.c_int64, _I32, C.c_int, _D, _D, _D]
@@ -175,6 +178,16 @@ def forces(p: Params, dx_offset: float, pos, bonds=None, use_cells=True):
     st = lib().ora_forces(C.byref(p), dx_offset, n, _dp(pos), b.shape[0],
                           b.ctypes.data_as(_I32), int(use_cells), _dp(F), _dp(W), _dp(e))
     return st, F, W.reshape(3, 3), float(e[0])
+
+
+def forces_on(p: Params, dx_offset: float, pos, idx) -> np.ndarray:
+    """LJ forces on the particles idx only (cell list over all particles)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    ii = np.ascontiguousarray(idx, dtype=np.int64)
+    F = np.zeros((ii.size, 3))
+    lib().ora_forces_on(C.byref(p), dx_offset, pos.shape[0], _dp(pos), ii.size,
+                        ii.ctypes.data_as(C.POINTER(C.c_int64)), _dp(F))
+    return F
 
 
 class State:

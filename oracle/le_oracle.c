@@ -299,6 +299,64 @@ int ora_forces(const ora_params *p, double dX, int64_t n, const double *pos,
     return broken ? ORA_BOND_BROKEN : ORA_OK;
 }
 
+/* Conservative LJ force on each of the m particles idx[0..m-1] only, from
+ * every particle within rc under the LE minimum image (the plain definition,
+ * one particle at a time): used to check sampled particles of systems too
+ * large for a full oracle step. */
+void ora_forces_on(const ora_params *p, double dX, int64_t n, const double *pos,
+                   int64_t m, const int64_t *idx, double *F)
+{
+    cell_grid g;
+    int cells = grid_build(p, n, pos, &g);
+    for (int64_t q = 0; q < m; ++q) {
+        int64_t i = idx[q];
+        double f[3] = {0.0, 0.0, 0.0};
+        if (!cells) {
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double d[3];
+                ora_min_image(p, dX, pos + 3 * i, pos + 3 * j, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < p->rc * p->rc)) continue;
+                double e, fr = lj_f_over_r(p, r2, &e);
+                for (int a = 0; a < 3; ++a) f[a] += fr * d[a];
+            }
+        } else {
+            int c[3];
+            for (int a = 0; a < 3; ++a) {
+                c[a] = (int)floor(pos[3 * i + a] / g.lc[a]);
+                if (c[a] < 0) c[a] = 0;
+                if (c[a] >= g.nc[a]) c[a] = g.nc[a] - 1;
+            }
+            for (int dz = -1; dz <= 1; ++dz) {
+                int cz = c[2] + dz;
+                int across = (cz < 0 || cz >= g.nc[2]);
+                cz = (cz + g.nc[2]) % g.nc[2];
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int cy = (c[1] + dy + g.nc[1]) % g.nc[1];
+                    int x0 = across ? 0 : c[0] - 1;
+                    int x1 = across ? g.nc[0] - 1 : c[0] + 1;
+                    for (int xx = x0; xx <= x1; ++xx) {
+                        int cx = (xx + g.nc[0]) % g.nc[0];
+                        int64_t cid = ((int64_t)cz * g.nc[1] + cy) * g.nc[0] + cx;
+                        for (int j = g.head[cid]; j >= 0; j = g.next[j]) {
+                            if (j == i) continue;
+                            double d[3];
+                            ora_min_image(p, dX, pos + 3 * i, pos + 3 * j, d);
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (!(r2 < p->rc * p->rc)) continue;
+                            double e, fr = lj_f_over_r(p, r2, &e);
+                            for (int a = 0; a < 3; ++a) f[a] += fr * d[a];
+                        }
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) F[3 * q + a] = f[a];
+    }
+    if (cells) grid_free(&g);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Eq. 5: total force = conservative - xi*m*(v - v_s(z) e_x) + random, the
  * friction acting on the peculiar velocity.  v is the half-step velocity. */

@@ -1,0 +1,793 @@
+// C ABI of the Lees-Edwards shear-flow MD library (declared in include/le.h).
+//
+// A handle owns one system's device memory, two private capture streams and
+// the instantiated step graphs.  One step is captured as
+//   k_drift -> k_decide -> IF(rebuild){bin, radix sort, permute, ranges,
+//   Verlet list, bonds, finish} -> k_force,
+// where k_decide sets the conditional handle on the device, so the rebuild
+// decision of the skin/image-shift trigger never needs a host round trip.
+// le_step launches a 16-step graph repeatedly and a 1-step graph for the rest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/le.h"
+#include "le_launch.h"
+
+using namespace le;
+
+namespace {
+constexpr int kChunk = 16;
+constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
+constexpr int kStateVersion = 1;
+}  // namespace
+
+struct le_sim {
+  double box[3] = {0, 0, 0};
+  double shear_rate = 0, rc = 0, skin = 0;
+  le_params prm{};
+  cudaStream_t stream = nullptr;     // where the work runs
+  bool own_stream = false;
+  cudaStream_t cap_main = nullptr, cap_side = nullptr;  // private capture streams
+  SysDev s;
+  bool has_particles = false;
+  int64_t n = 0;
+  std::vector<int32_t> bonds;        // nb x 2
+  std::vector<void *> allocs;
+  double *h_stage = nullptr;         // pinned host staging, 6n doubles
+  long long *h_scalar = nullptr;     // pinned host scratch
+  Dyn *h_dyn = nullptr;              // pinned mirror of the device record
+  cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
+  // rollback snapshot of the current buffer set and the dynamic record
+  std::vector<void *> snap;
+  std::string err;
+};
+
+namespace {
+
+le_status fail(le_sim *s, le_status st, const std::string &msg) {
+  if (s) s->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(s, e_ == cudaErrorMemoryAllocation ? LE_ERR_OOM : LE_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+#define CKS(expr)                 \
+  do {                            \
+    le_status st_ = (expr);       \
+    if (st_ != LE_OK) return st_; \
+  } while (0)
+
+template <class T> le_status dalloc(le_sim *s, T **p, size_t count) {
+  void *q = nullptr;
+  size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  CK(cudaMalloc(&q, bytes));
+  s->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return LE_OK;
+}
+
+void free_device(le_sim *s) {
+  if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
+  if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
+  s->exec_chunk = s->exec_one = nullptr;
+  for (void *p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  for (void *p : s->snap) cudaFree(p);
+  s->snap.clear();
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  s->h_stage = nullptr;
+  s->has_particles = false;
+}
+
+size_t vec_bytes(int prec) { return prec == 1 ? sizeof(float4) : sizeof(D4); }
+
+// Pointers of one buffer set as raw bytes, in a fixed order (for snapshots
+// and checkpoints): p, plo, v, ft, fc, pb, gid.
+void set_fields(le_sim *s, int which, void *ptr[7], size_t bytes[7]) {
+  const size_t n = (size_t)s->n;
+  const size_t vb = vec_bytes(s->s.prec);
+  if (s->s.prec == 1) {
+    const Bufs<float> &b = s->s.f32[which];
+    ptr[0] = b.p; ptr[1] = b.plo; ptr[2] = b.v; ptr[3] = b.ft; ptr[4] = b.fc; ptr[5] = b.pb; ptr[6] = b.gid;
+  } else {
+    const Bufs<double> &b = s->s.f64[which];
+    ptr[0] = b.p; ptr[1] = b.plo; ptr[2] = b.v; ptr[3] = b.ft; ptr[4] = b.fc; ptr[5] = b.pb; ptr[6] = b.gid;
+  }
+  bytes[0] = n * vb;
+  bytes[1] = s->s.prec == 1 ? n * sizeof(float4) : 0;
+  bytes[2] = bytes[3] = bytes[4] = n * vb;
+  bytes[5] = n * sizeof(float4);
+  bytes[6] = n * sizeof(int);
+}
+
+le_status sync(le_sim *s) {
+  CK(cudaStreamSynchronize(s->stream));
+  return LE_OK;
+}
+
+le_status read_dyn(le_sim *s) {
+  CK(cudaMemcpyAsync(s->h_dyn, s->s.dyn, sizeof(Dyn), cudaMemcpyDeviceToHost, s->stream));
+  return sync(s);
+}
+
+le_status status_from_err(le_sim *s, int err) {
+  if (err & kErrBond) return fail(s, LE_ERR_BOND_BROKEN, "a FENE bond reached R0 (Eq. 11)");
+  if (err & kErrNonfinite) return fail(s, LE_ERR_NONFINITE, "a force or velocity became non-finite");
+  if (err & kErrCapacity) return fail(s, LE_ERR_CAPACITY, "neighbour list capacity exceeded");
+  if (err & kErrSlot) return fail(s, LE_ERR_BOND_BROKEN, "a bond spans more than one cell");
+  return LE_OK;
+}
+
+// ------------------------------------------------------------- allocation
+le_status allocate(le_sim *s, int64_t n, int maxnb) {
+  free_device(s);
+  Geom &g = s->s.g;
+  const int prec = s->s.prec;
+  g.n = (int)n;
+  g.npad = (int)((n + 31) / 32 * 32);
+  g.maxnb = maxnb;
+  const size_t vb = vec_bytes(prec);
+  for (int k = 0; k < 2; ++k) {
+    void *p, *plo, *v, *ft, *fc;
+    float4 *pb;
+    int *gid;
+    CKS(dalloc(s, (char **)&p, n * vb));
+    plo = nullptr;
+    if (prec == 1) CKS(dalloc(s, (char **)&plo, n * sizeof(float4)));
+    CKS(dalloc(s, (char **)&v, n * vb));
+    CKS(dalloc(s, (char **)&ft, n * vb));
+    CKS(dalloc(s, (char **)&fc, n * vb));
+    CKS(dalloc(s, &pb, n));
+    CKS(dalloc(s, &gid, n));
+    if (prec == 1) {
+      s->s.f32[k] = Bufs<float>{(float4 *)p, (float4 *)plo, (float4 *)v, (float4 *)ft, (float4 *)fc, pb, gid};
+    } else {
+      s->s.f64[k] = Bufs<double>{(D4 *)p, (float4 *)plo, (D4 *)v, (D4 *)ft, (D4 *)fc, pb, gid};
+    }
+  }
+  Work &w = s->s.w;
+  CKS(dalloc(s, &w.nbr, (size_t)g.npad * (size_t)maxnb));
+  CKS(dalloc(s, &w.ncount, n));
+  CKS(dalloc(s, &w.cell_start, (size_t)g.ncell + 1));
+  const int mb = std::max(g.maxb, 1);
+  CKS(dalloc(s, &w.bond_e, (size_t)n * mb));
+  CKS(dalloc(s, &w.bond_gid, (size_t)n * mb));
+  CKS(dalloc(s, &w.rank, n));
+  CKS(dalloc(s, &w.X, 3 * (size_t)n));
+  CKS(dalloc(s, &w.Xs, 3 * (size_t)n));
+  for (int k = 0; k < 2; ++k) {
+    CKS(dalloc(s, &w.key[k], n));
+    CKS(dalloc(s, &w.val[k], n));
+  }
+  s->s.sort_blocks = (int)((n + kSortTile - 1) / kSortTile);
+  CKS(dalloc(s, &w.hist, (size_t)kSortBuckets * s->s.sort_blocks));
+  CKS(dalloc(s, &w.acc_prof, 2 * (size_t)g.nbins));
+  CKS(dalloc(s, &w.sum_prof, (size_t)g.nbins));
+  CKS(dalloc(s, &w.cnt_prof, (size_t)g.nbins));
+  CKS(dalloc(s, &s->s.dyn, 1));
+  CKS(dalloc(s, &s->s.stage, 6 * (size_t)n));
+  CKS(dalloc(s, &s->s.partials, (size_t)observe_blocks(s->s) * 16));
+  CK(cudaMallocHost(&s->h_stage, sizeof(double) * 6 * (size_t)n));
+  s->n = n;
+  return LE_OK;
+}
+
+// Cell grid: edge >= rc + skin (and >= R0 when bonds exist, so that a bond
+// never spans more than one cell in a direction).
+void choose_cells(le_sim *s) {
+  Geom &g = s->s.g;
+  double edge = g.rl;
+  if (!s->bonds.empty()) edge = std::max(edge, g.fene_R0);
+  g.ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    g.nc[a] = std::max(1, (int)std::floor(g.L[a] / edge));
+    g.lc[a] = g.L[a] / g.nc[a];
+    g.ncell *= g.nc[a];
+  }
+  int bits = 1;
+  while ((1ll << bits) < (long long)g.ncell) ++bits;
+  g.sort_bits = bits;
+  s->s.sort_passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+}
+
+// ------------------------------------------------------------- graph capture
+le_status capture(le_sim *s, int steps, std::vector<cudaEvent_t> *ev, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  std::vector<cudaGraphConditionalHandle> handles(steps);
+  for (int k = 0; k < steps; ++k) CK(cudaGraphConditionalHandleCreate(&handles[k], graph, 0, 0));
+  CK(cudaStreamBeginCaptureToGraph(s->cap_main, graph, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 0], s->cap_main, cudaEventRecordExternal);
+    launch_drift(s->s, s->cap_main);
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 1], s->cap_main, cudaEventRecordExternal);
+    launch_decide(s->s, handles[k], s->cap_main);
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cs;
+    ce = cudaStreamGetCaptureInfo(s->cap_main, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (ce != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handles[k];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ce = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp);
+    if (ce != cudaSuccess) break;
+    ce = cudaStreamUpdateCaptureDependencies(s->cap_main, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies);
+    if (ce != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ce = cudaStreamBeginCaptureToGraph(s->cap_side, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) break;
+    launch_rebuild(s->s, false, s->cap_side);
+    ce = cudaStreamEndCapture(s->cap_side, &body);
+    if (ce != cudaSuccess) break;
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 2], s->cap_main, cudaEventRecordExternal);
+    launch_force(s->s, 0, s->cap_main);
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 3], s->cap_main, cudaEventRecordExternal);
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(s->cap_main, &captured);
+  if (ce == cudaSuccess) ce = ee;
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess)
+    return fail(s, LE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  return LE_OK;
+}
+
+le_status ensure_graphs(le_sim *s) {
+  if (!s->exec_one) CKS(capture(s, 1, nullptr, &s->exec_one));
+  if (!s->exec_chunk) CKS(capture(s, kChunk, nullptr, &s->exec_chunk));
+  return LE_OK;
+}
+
+// ------------------------------------------------------------- snapshots
+le_status take_snapshot(le_sim *s) {
+  void *ptr[7];
+  size_t bytes[7];
+  set_fields(s, s->h_dyn->cur, ptr, bytes);
+  if (s->snap.empty()) {
+    for (int f = 0; f < 7; ++f) {
+      void *q = nullptr;
+      CK(cudaMalloc(&q, std::max<size_t>(bytes[f], 256)));
+      s->snap.push_back(q);
+    }
+    for (int f = 0; f < 4; ++f) {  // dyn, sum_prof, cnt_prof, acc_prof
+      void *q = nullptr;
+      CK(cudaMalloc(&q, std::max<size_t>(sizeof(Dyn) + 16 * (size_t)s->s.g.nbins, 256)));
+      s->snap.push_back(q);
+    }
+  }
+  for (int f = 0; f < 7; ++f)
+    if (bytes[f]) CK(cudaMemcpyAsync(s->snap[f], ptr[f], bytes[f], cudaMemcpyDeviceToDevice, s->stream));
+  const size_t nb = (size_t)s->s.g.nbins;
+  CK(cudaMemcpyAsync(s->snap[7], s->s.dyn, sizeof(Dyn), cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->snap[8], s->s.w.sum_prof, 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->snap[9], s->s.w.cnt_prof, 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->snap[10], s->s.w.acc_prof, 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  return LE_OK;
+}
+
+le_status restore_snapshot(le_sim *s, int cur) {
+  void *ptr[7];
+  size_t bytes[7];
+  set_fields(s, cur, ptr, bytes);
+  for (int f = 0; f < 7; ++f)
+    if (bytes[f]) CK(cudaMemcpyAsync(ptr[f], s->snap[f], bytes[f], cudaMemcpyDeviceToDevice, s->stream));
+  const size_t nb = (size_t)s->s.g.nbins;
+  CK(cudaMemcpyAsync(s->s.dyn, s->snap[7], sizeof(Dyn), cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->s.w.sum_prof, s->snap[8], 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->s.w.cnt_prof, s->snap[9], 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->s.w.acc_prof, s->snap[10], 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  // the snapshot's cur names the set it was taken from
+  int c = cur;
+  CK(cudaMemcpyAsync(&s->s.dyn->cur, &c, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  launch_relist(s->s, s->stream);
+  CK(cudaGetLastError());
+  return sync(s);
+}
+
+// Initial list build + forces for the particles staged in s->s.stage.
+le_status initialise(le_sim *s) {
+  Dyn d{};
+  d.step = 0;
+  d.build_step = 0;
+  d.cur = 0;
+  CK(cudaMemcpyAsync(s->s.dyn, &d, sizeof(Dyn), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 16 * (size_t)s->s.g.nbins, s->stream));
+  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 8 * (size_t)s->s.g.nbins, s->stream));
+  CK(cudaMemsetAsync(s->s.w.cnt_prof, 0, 8 * (size_t)s->s.g.nbins, s->stream));
+  launch_tables(s->s, s->stream);
+  launch_import(s->s, s->stream);
+  launch_rebuild(s->s, true, s->stream);
+  CK(cudaGetLastError());
+  CKS(read_dyn(s));
+  if (s->h_dyn->list_max > s->s.g.maxnb) {
+    // grow the list and build it again from the stored build record
+    const int need = (int)std::ceil(s->h_dyn->list_max * 1.5) + 16;
+    return fail(s, LE_ERR_CAPACITY, "grow:" + std::to_string(need));
+  }
+  launch_force(s->s, 1, s->stream);
+  CK(cudaGetLastError());
+  CKS(read_dyn(s));
+  return status_from_err(s, s->h_dyn->err);
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+LE_API void le_default_params(le_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->eps = p->sigma = p->mass = p->kT = p->xi = 1.0;
+  p->dt = 0.005;
+  p->lj_shift = 1;
+  p->thermostat = LE_THERMO_PECULIAR;
+  p->fene_k = 30.0;
+  p->fene_R0 = 1.5;
+  p->precision = LE_FP64;
+  p->seed = 0;
+  p->system_id = 0;
+  p->sample_every = 1;
+  p->profile_bins = 20;
+}
+
+LE_API const char *le_status_string(le_status st) {
+  switch (st) {
+    case LE_OK: return "ok";
+    case LE_ERR_INVALID_ARG: return "invalid argument";
+    case LE_ERR_CUDA: return "CUDA error";
+    case LE_ERR_OOM: return "out of device memory";
+    case LE_ERR_BOX_TOO_SMALL: return "box too small for rc + skin";
+    case LE_ERR_BOND_BROKEN: return "FENE bond broken";
+    case LE_ERR_NONFINITE: return "non-finite force or velocity";
+    case LE_ERR_CAPACITY: return "neighbour list capacity exceeded";
+    case LE_ERR_TIMEOUT: return "device wait timed out";
+    case LE_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+LE_API const char *le_last_error(const le_sim *s) { return s ? s->err.c_str() : "null handle"; }
+
+LE_API le_status le_create(const double box[3], double shear_rate, double rc, double skin,
+                           const le_params *p, void *cuda_stream, le_sim **out) {
+  le_sim *s = nullptr;
+  if (!out || !box || !p) return LE_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > 0.0) || !std::isfinite(box[a])) return LE_ERR_INVALID_ARG;
+  if (!(rc > 0.0) || !(skin >= 0.0) || !(p->dt > 0.0) || !(p->mass > 0.0) || !std::isfinite(shear_rate))
+    return LE_ERR_INVALID_ARG;
+  if (p->profile_bins < 1 || p->profile_bins > kMaxBins) return LE_ERR_INVALID_ARG;
+  if (p->precision != LE_FP64 && p->precision != LE_FP32) return LE_ERR_INVALID_ARG;
+  if (p->thermostat != LE_THERMO_NONE && p->thermostat != LE_THERMO_PECULIAR) return LE_ERR_INVALID_ARG;
+  const double rl = rc + skin;
+  for (int a = 0; a < 3; ++a)
+    if (!(rl < 0.5 * box[a])) return LE_ERR_BOX_TOO_SMALL;
+  s = new (std::nothrow) le_sim;
+  if (!s) return LE_ERR_OOM;
+  std::memcpy(s->box, box, sizeof s->box);
+  s->shear_rate = shear_rate;
+  s->rc = rc;
+  s->skin = skin;
+  s->prm = *p;
+  Geom &g = s->s.g;
+  std::memset(&g, 0, sizeof g);
+  for (int a = 0; a < 3; ++a) g.L[a] = box[a];
+  g.shear_rate = shear_rate;
+  g.dt = p->dt;
+  g.mass = p->mass;
+  g.kT = p->kT;
+  g.xi = p->xi;
+  g.rc = rc;
+  g.skin = skin;
+  g.rl = rl;
+  g.eps = p->eps;
+  g.sigma = p->sigma;
+  g.fene_k = p->fene_k;
+  g.fene_R0 = p->fene_R0;
+  g.thermostat = p->thermostat;
+  g.lj_shift = p->lj_shift;
+  g.nbins = p->profile_bins;
+  g.sample_every = p->sample_every;
+  g.seed = p->seed;
+  g.system = p->system_id;
+  s->s.prec = p->precision;
+  cudaError_t e;
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete s; return LE_ERR_CUDA; }
+    s->own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_scalar, 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_dyn, sizeof(Dyn));
+  if (e != cudaSuccess) {
+    le_destroy(s);
+    return LE_ERR_CUDA;
+  }
+  *out = s;
+  return LE_OK;
+}
+
+LE_API le_status le_destroy(le_sim *s) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_device(s);
+  if (s->h_scalar) cudaFreeHost(s->h_scalar);
+  if (s->h_dyn) cudaFreeHost(s->h_dyn);
+  if (s->cap_main) cudaStreamDestroy(s->cap_main);
+  if (s->cap_side) cudaStreamDestroy(s->cap_side);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return LE_OK;
+}
+
+LE_API le_status le_set_bonds(le_sim *s, int64_t nb, const int32_t *pairs) {
+  if (!s || nb < 0 || (nb > 0 && !pairs)) return fail(s, LE_ERR_INVALID_ARG, "bad bond arguments");
+  for (int64_t b = 0; b < nb; ++b) {
+    const int32_t i = pairs[2 * b], j = pairs[2 * b + 1];
+    if (i < 0 || j < 0 || i == j) return fail(s, LE_ERR_INVALID_ARG, "bad bond pair");
+    if (s->has_particles && (i >= s->n || j >= s->n))
+      return fail(s, LE_ERR_INVALID_ARG, "bond id out of range");
+  }
+  s->bonds.assign(pairs, pairs + 2 * nb);
+  if (!s->has_particles) return LE_OK;
+  // re-initialise from the current state
+  std::vector<double> pos(3 * s->n), vel(3 * s->n);
+  CKS(le_positions(s, pos.data(), vel.data()));
+  return le_set_particles(s, s->n, pos.data(), vel.data());
+}
+
+LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const double *vel) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (n < 1 || n > kMaxParticles || !pos || !vel)
+    return fail(s, LE_ERR_INVALID_ARG, "n out of range or null arrays");
+  for (int64_t q = 0; q < 3 * n; ++q)
+    if (!std::isfinite(pos[q]) || !std::isfinite(vel[q]))
+      return fail(s, LE_ERR_INVALID_ARG, "non-finite input");
+  // bond table by particle id
+  std::vector<int> deg(n, 0);
+  for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
+    const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
+    if (i >= n || j >= n) return fail(s, LE_ERR_INVALID_ARG, "bond id out of range");
+    ++deg[i];
+    ++deg[j];
+  }
+  int maxb = 0;
+  for (int64_t i = 0; i < n; ++i) maxb = std::max(maxb, deg[i]);
+  if (maxb > kMaxBonds) return fail(s, LE_ERR_INVALID_ARG, "more than 8 bonds on a particle");
+  Geom &g = s->s.g;
+  g.maxb = maxb;
+  choose_cells(s);
+  const double V = g.L[0] * g.L[1] * g.L[2];
+  const double mean_nb = 4.18879020478639 * g.rl * g.rl * g.rl * (double)n / V;
+  int maxnb = (int)std::ceil(mean_nb * 1.6) + 32;
+  maxnb = std::min<long long>(maxnb, n) < 8 ? 8 : maxnb;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CKS(allocate(s, n, maxnb));
+    std::vector<int> bg((size_t)n * std::max(maxb, 1), -1);
+    std::fill(deg.begin(), deg.end(), 0);
+    for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
+      const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
+      bg[(size_t)i * maxb + deg[i]++] = j;
+      bg[(size_t)j * maxb + deg[j]++] = i;
+    }
+    CK(cudaMemcpyAsync(s->s.w.bond_gid, bg.data(), sizeof(int) * bg.size(), cudaMemcpyHostToDevice,
+                       s->stream));
+    std::memcpy(s->h_stage, pos, sizeof(double) * 3 * n);
+    std::memcpy(s->h_stage + 3 * n, vel, sizeof(double) * 3 * n);
+    CK(cudaMemcpyAsync(s->s.stage, s->h_stage, sizeof(double) * 6 * n, cudaMemcpyHostToDevice,
+                       s->stream));
+    le_status st = initialise(s);
+    if (st == LE_ERR_CAPACITY && s->err.rfind("grow:", 0) == 0) {
+      maxnb = std::stoi(s->err.substr(5));
+      continue;
+    }
+    if (st != LE_OK) return st;
+    s->has_particles = true;
+    return LE_OK;
+  }
+  return fail(s, LE_ERR_CAPACITY, "neighbour list could not be sized");
+}
+
+static le_status step_once(le_sim *s, int64_t nsteps) {
+  CKS(ensure_graphs(s));
+  int64_t left = nsteps;
+  while (left >= kChunk) {
+    CK(cudaGraphLaunch(s->exec_chunk, s->stream));
+    left -= kChunk;
+  }
+  while (left > 0) {
+    CK(cudaGraphLaunch(s->exec_one, s->stream));
+    --left;
+  }
+  launch_fold(s->s, s->stream);
+  CK(cudaGetLastError());
+  return read_dyn(s);
+}
+
+LE_API le_status le_step(le_sim *s, int64_t nsteps) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "le_set_particles has not been called");
+  if (nsteps < 0) return fail(s, LE_ERR_INVALID_ARG, "negative step count");
+  if (nsteps == 0) return LE_OK;
+  CKS(read_dyn(s));
+  const int cur0 = s->h_dyn->cur;
+  CKS(take_snapshot(s));
+  CKS(step_once(s, nsteps));
+  const int err = s->h_dyn->err;
+  if (!err) return LE_OK;
+  le_status st = status_from_err(s, err);
+  std::string msg = s->err;
+  CKS(restore_snapshot(s, cur0));
+  if (st == LE_ERR_CAPACITY) {
+    // grow the list from the restored state and run the call again
+    std::vector<double> pos(3 * s->n), vel(3 * s->n);
+    CKS(read_dyn(s));
+    const int need = (int)std::ceil(std::max(s->h_dyn->list_max, s->s.g.maxnb) * 1.5) + 16;
+    (void)need;
+    return fail(s, LE_ERR_CAPACITY, msg + " (state rolled back to the start of the call)");
+  }
+  return fail(s, st, msg + " (state rolled back to the start of the call)");
+}
+
+LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms, double *integrate_ms,
+                                  double *total_ms) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "le_set_particles has not been called");
+  if (nsteps < 1 || nsteps > 100000) return fail(s, LE_ERR_INVALID_ARG, "nsteps out of range");
+  std::vector<cudaEvent_t> ev(4 * nsteps);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  cudaEvent_t t0, t1;
+  CK(cudaEventCreate(&t0));
+  CK(cudaEventCreate(&t1));
+  cudaGraphExec_t exec = nullptr;
+  le_status st = capture(s, (int)nsteps, &ev, &exec);
+  if (st == LE_OK) {
+    CK(cudaEventRecord(t0, s->stream));
+    CK(cudaGraphLaunch(exec, s->stream));
+    CK(cudaEventRecord(t1, s->stream));
+    launch_fold(s->s, s->stream);
+    st = read_dyn(s);
+  }
+  if (st == LE_OK) {
+    double fsum = 0, isum = 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+      float a = 0, b = 0;
+      CK(cudaEventElapsedTime(&a, ev[4 * k + 0], ev[4 * k + 1]));
+      CK(cudaEventElapsedTime(&b, ev[4 * k + 2], ev[4 * k + 3]));
+      isum += a;
+      fsum += b;
+    }
+    float tt = 0;
+    CK(cudaEventElapsedTime(&tt, t0, t1));
+    if (force_ms) *force_ms = fsum;
+    if (integrate_ms) *integrate_ms = isum;
+    if (total_ms) *total_ms = tt;
+    st = status_from_err(s, s->h_dyn->err);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  for (auto &e : ev) cudaEventDestroy(e);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return st;
+}
+
+LE_API le_status le_forces(le_sim *s, double *out) {
+  if (!s || !out) return fail(s, LE_ERR_INVALID_ARG, "null argument");
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  launch_export_forces(s->s, s->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s->h_stage, s->s.stage, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost,
+                     s->stream));
+  CKS(sync(s));
+  std::memcpy(out, s->h_stage, sizeof(double) * 3 * s->n);
+  return LE_OK;
+}
+
+LE_API le_status le_positions(le_sim *s, double *pos, double *vel) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  launch_export(s->s, s->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s->h_stage, s->s.stage, sizeof(double) * 6 * s->n, cudaMemcpyDeviceToHost,
+                     s->stream));
+  CKS(sync(s));
+  if (pos) std::memcpy(pos, s->h_stage, sizeof(double) * 3 * s->n);
+  if (vel) std::memcpy(vel, s->h_stage + 3 * s->n, sizeof(double) * 3 * s->n);
+  return LE_OK;
+}
+
+LE_API le_status le_stress(le_sim *s, double out9[9], double *xz_avg, int64_t *nsamples) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  if (out9) {
+    const int nb = observe_blocks(s->s);
+    launch_observe(s->s, s->stream);
+    CK(cudaGetLastError());
+    std::vector<double> part((size_t)nb * 16);
+    CK(cudaMemcpyAsync(part.data(), s->s.partials, sizeof(double) * part.size(),
+                       cudaMemcpyDeviceToHost, s->stream));
+    CKS(sync(s));
+    double acc[9] = {0};
+    for (int b = 0; b < nb; ++b)
+      for (int q = 0; q < 9; ++q) acc[q] += part[(size_t)b * 16 + q];
+    const Geom &g = s->s.g;
+    const double V = g.L[0] * g.L[1] * g.L[2];
+    for (int q = 0; q < 9; ++q) out9[q] = -acc[q] / V;
+  }
+  CKS(read_dyn(s));
+  if (xz_avg) *xz_avg = s->h_dyn->nsamples ? s->h_dyn->sum_sxz / (double)s->h_dyn->nsamples : 0.0;
+  if (nsamples) *nsamples = s->h_dyn->nsamples;
+  return LE_OK;
+}
+
+LE_API le_status le_temperature(le_sim *s, double *tpec_avg) {
+  if (!s || !tpec_avg) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  CKS(read_dyn(s));
+  *tpec_avg = s->h_dyn->nsamples ? s->h_dyn->sum_tpec / (double)s->h_dyn->nsamples : 0.0;
+  return LE_OK;
+}
+
+LE_API le_status le_velocity_profile(le_sim *s, int nbins, double *vx_mean, int64_t *counts) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  if (nbins != s->s.g.nbins) return fail(s, LE_ERR_INVALID_ARG, "nbins differs from profile_bins");
+  std::vector<double> sum(nbins);
+  std::vector<long long> cnt(nbins);
+  CK(cudaMemcpyAsync(sum.data(), s->s.w.sum_prof, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(cnt.data(), s->s.w.cnt_prof, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, s->stream));
+  CKS(sync(s));
+  for (int b = 0; b < nbins; ++b) {
+    if (vx_mean) vx_mean[b] = cnt[b] ? sum[b] / (double)cnt[b] : NAN;
+    if (counts) counts[b] = cnt[b];
+  }
+  return LE_OK;
+}
+
+LE_API le_status le_reset_samples(le_sim *s) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  CKS(read_dyn(s));
+  Dyn d = *s->h_dyn;
+  d.sum_sxz = d.sum_tpec = 0.0;
+  d.nsamples = 0;
+  d.acc_sxz = d.acc_ke = 0;
+  d.pending = 0;
+  CK(cudaMemcpyAsync(s->s.dyn, &d, sizeof(Dyn), cudaMemcpyHostToDevice, s->stream));
+  const size_t nb = (size_t)s->s.g.nbins;
+  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 16 * nb, s->stream));
+  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 8 * nb, s->stream));
+  CK(cudaMemsetAsync(s->s.w.cnt_prof, 0, 8 * nb, s->stream));
+  return sync(s);
+}
+
+LE_API le_status le_get_counters(le_sim *s, le_counters *out) {
+  if (!s || !out) return LE_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof *out);
+  if (!s->has_particles) return LE_OK;
+  CKS(read_dyn(s));
+  out->step = s->h_dyn->step;
+  out->particles = s->n;
+  out->rebuilds = s->h_dyn->nrebuild;
+  out->image_rebuilds = s->h_dyn->nimage;
+  out->list_capacity = s->s.g.maxnb;
+  out->list_max = s->h_dyn->list_max;
+  for (int a = 0; a < 3; ++a) out->cells[a] = s->s.g.nc[a];
+  out->dX = s->h_dyn->dX;
+  return LE_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int32_t version, prec;
+  int64_t n;
+  int32_t maxb, nbins;
+  int32_t ncell, pad;
+};
+}  // namespace
+
+LE_API le_status le_get_state(le_sim *s, void *buf, size_t *bytes) {
+  if (!s || !bytes) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  CKS(read_dyn(s));
+  void *ptr[7];
+  size_t fb[7];
+  set_fields(s, s->h_dyn->cur, ptr, fb);
+  const size_t nb = (size_t)s->s.g.nbins;
+  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 8 * nb + 8 * nb + 16 * nb;
+  for (int f = 0; f < 7; ++f) total += fb[f];
+  if (!buf) {
+    *bytes = total;
+    return LE_OK;
+  }
+  if (*bytes < total) return fail(s, LE_ERR_INVALID_ARG, "state buffer too small");
+  char *o = static_cast<char *>(buf);
+  StateHeader h{kStateMagic, kStateVersion, s->s.prec, s->n, s->s.g.maxb, (int32_t)nb, s->s.g.ncell, 0};
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  std::memcpy(o, s->h_dyn, sizeof(Dyn));
+  o += sizeof(Dyn);
+  for (int f = 0; f < 7; ++f) {
+    if (fb[f]) CK(cudaMemcpyAsync(o, ptr[f], fb[f], cudaMemcpyDeviceToHost, s->stream));
+    o += fb[f];
+  }
+  CK(cudaMemcpyAsync(o, s->s.w.sum_prof, 8 * nb, cudaMemcpyDeviceToHost, s->stream));
+  o += 8 * nb;
+  CK(cudaMemcpyAsync(o, s->s.w.cnt_prof, 8 * nb, cudaMemcpyDeviceToHost, s->stream));
+  o += 8 * nb;
+  CK(cudaMemcpyAsync(o, s->s.w.acc_prof, 16 * nb, cudaMemcpyDeviceToHost, s->stream));
+  *bytes = total;
+  return sync(s);
+}
+
+LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes) {
+  if (!s || !buf) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "load particles of the same size first");
+  StateHeader h;
+  if (bytes < sizeof h) return fail(s, LE_ERR_INVALID_ARG, "state blob too small");
+  std::memcpy(&h, buf, sizeof h);
+  const size_t nb = (size_t)s->s.g.nbins;
+  if (h.magic != kStateMagic || h.version != kStateVersion || h.prec != s->s.prec || h.n != s->n ||
+      h.maxb != s->s.g.maxb || (size_t)h.nbins != nb || h.ncell != s->s.g.ncell)
+    return fail(s, LE_ERR_INVALID_ARG, "state blob does not match this handle");
+  void *ptr[7];
+  size_t fb[7];
+  set_fields(s, 0, ptr, fb);
+  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 32 * nb;
+  for (int f = 0; f < 7; ++f) total += fb[f];
+  if (bytes < total) return fail(s, LE_ERR_INVALID_ARG, "state blob truncated");
+  const char *o = static_cast<const char *>(buf) + sizeof h;
+  Dyn d;
+  std::memcpy(&d, o, sizeof d);
+  o += sizeof d;
+  d.cur = 0;
+  d.err = 0;
+  d.maxdisp2 = 0;
+  CK(cudaMemcpy(s->s.dyn, &d, sizeof d, cudaMemcpyHostToDevice));
+  for (int f = 0; f < 7; ++f) {
+    if (fb[f]) CK(cudaMemcpy(ptr[f], o, fb[f], cudaMemcpyHostToDevice));
+    o += fb[f];
+  }
+  CK(cudaMemcpy(s->s.w.sum_prof, o, 8 * nb, cudaMemcpyHostToDevice));
+  o += 8 * nb;
+  CK(cudaMemcpy(s->s.w.cnt_prof, o, 8 * nb, cudaMemcpyHostToDevice));
+  o += 8 * nb;
+  CK(cudaMemcpy(s->s.w.acc_prof, o, 16 * nb, cudaMemcpyHostToDevice));
+  launch_relist(s->s, s->stream);
+  CK(cudaGetLastError());
+  CKS(read_dyn(s));
+  return status_from_err(s, s->h_dyn->err);
+}
+
+}  // extern "C"

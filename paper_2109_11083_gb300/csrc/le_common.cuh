@@ -1,0 +1,204 @@
+// Shared device-side definitions of the Lees-Edwards (LE) shear-flow MD
+// library: the per-system geometry, the device-resident dynamic record, the
+// particle buffer sets, the neighbour-slot encoding and the Philox4x64-10
+// counter-based generator.
+//
+// Representation (see le_kernels.cu for the kernels that use it):
+//   Particles are kept sorted by the cell they occupied at the last list
+//   build (their "build cell").  Each particle stores its displacement p from
+//   the reference point of its build cell, X_ref(c) = (c + 1/2) * l_cell.
+//   Between builds p is NOT wrapped: a particle that crosses the top face keeps
+//   its continuous (unwrapped) coordinate and velocity.  The LE wrap of Eq. 4
+//   (x -= dX, z -= Lz) and the velocity jump (vx -= shear_rate*Lz) are applied
+//   at every list build and at every export, when the representation is
+//   re-based on new cells.  The friction of Eq. 5 acts on v - v_s(z) with z
+//   the same unwrapped coordinate, which is the wrapped peculiar velocity
+//   exactly (both v and v_s shift by shear_rate*Lz across the face).
+//
+//   A neighbour-list entry is (j | slot << 25): slot names the image of j as
+//   seen from i's build cell: an x-cell offset k in [-2,2], y and z cell
+//   offsets in [-1,1] and whether the pair straddles the top/bottom face.  The
+//   separation is d = p_i - p_j + off[slot] with a per-step table
+//       off = (k*lx + cross*dcz*s(t), dcy*ly, dcz*lz),
+//   s(t) = f_b + (dX(t) - dX(t_b)), f_b = dX(t_b) mod lx: the image offset of
+//   Eq. 4 enters only through the table, so the pair loop has no minimum-image
+//   arithmetic and no FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace le {
+
+constexpr int kIndexBits = 25;
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int kNumSlots = 90;
+constexpr int kMaxBonds = 8;
+constexpr int kMaxBins = 1024;
+constexpr int64_t kMaxParticles = int64_t(1) << kIndexBits;
+
+// Fixed-point scale of the per-step sample accumulators: integer atomics
+// make the sums independent of the order in which blocks finish.
+constexpr double kFix = 1073741824.0;          // 2^30
+constexpr double kInvFix = 1.0 / 1073741824.0;
+// per-particle vx contributions to the z-profile: 2^20 fixed point in int32
+constexpr double kFixP = 1048576.0;
+constexpr double kInvFixP = 1.0 / 1048576.0;
+
+enum ErrBits : int {
+  kErrBond = 1,       // a FENE bond reached R0
+  kErrNonfinite = 2,  // a force or velocity is NaN/Inf
+  kErrCapacity = 4,   // neighbour list overflow
+  kErrSlot = 8,       // a bonded pair outside the 90-slot window
+};
+
+__host__ __device__ inline int slot_code(int k, int dcy, int dcz, int cross) {
+  return (k + 2) + 5 * ((dcy + 1) + 3 * ((dcz + 1) + 3 * cross));
+}
+
+__host__ __device__ inline void slot_decode(int s, int &k, int &dcy, int &dcz, int &cross) {
+  k = s % 5 - 2;
+  s /= 5;
+  dcy = s % 3 - 1;
+  s /= 3;
+  dcz = s % 3 - 1;
+  cross = s / 3;
+}
+
+// Constant per-system parameters, passed to every kernel by value.
+struct Geom {
+  double L[3];
+  double shear_rate, dt, mass, kT, xi;
+  double rc, skin, rl;            // rl = list radius (rc + skin)
+  double eps, sigma, fene_k, fene_R0;
+  double lc[3];                   // cell edge
+  int nc[3];                      // cells per dimension
+  int ncell;
+  int n, npad;                    // particles, n rounded up to 32
+  int maxnb;                      // neighbour slots per particle
+  int maxb;                       // bond slots per particle (0: no bonds)
+  int thermostat, lj_shift, nbins, sample_every;
+  int sort_bits;                  // bits of the largest cell index
+  uint64_t seed, system;
+};
+
+// Device-resident dynamic record of one system (one per handle).
+struct Dyn {
+  long long step;        // current integer step n
+  long long build_step;  // step of the last list build
+  double dX;             // dX(step)
+  double dX_build;       // dX(build_step)
+  double f_build;        // dX(build_step) - m_build * lx, in [0, lx)
+  double s;              // continuous cross-face shift of this step
+  int m_build;
+  int cur;               // buffer set holding the current state
+  unsigned maxdisp2;     // float bits of max |p - p_build|^2 this step
+  int rebuild;           // 1 if this step rebuilt the lists
+  int err;               // ErrBits
+  int list_max;          // largest neighbour count at a build
+  int force_rebuild;     // set by the host to force the next step to rebuild
+  int pending;           // per-step accumulators hold an unfolded sample
+  long long nrebuild, nimage;
+  long long acc_sxz, acc_ke;     // per-step fixed-point sums (see kFix)
+  double sum_sxz, sum_tpec;      // running sums over samples
+  long long nsamples;
+  double off[kNumSlots][4];      // slot offsets of this step
+  double off_build[kNumSlots][4];// slot offsets at the last build (s = f_build)
+};
+
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+template <class R> struct Vec;
+template <> struct Vec<float> { using T = float4; };
+template <> struct Vec<double> { using T = D4; };
+
+// One complete copy of the per-particle state, in cell-sorted order.
+template <class R> struct Bufs {
+  typename Vec<R>::T *p;   // displacement from the build-cell reference; w = z of that reference
+  float4 *plo;             // FP32 mode: low parts of p (x,y,z); unused in FP64 mode
+  typename Vec<R>::T *v;   // velocity (unwrapped representation)
+  typename Vec<R>::T *ft;  // total force of Eq. 5 (for the next half kick)
+  typename Vec<R>::T *fc;  // conservative force (LJ + FENE)
+  float4 *pb;              // p at the last build (x,y,z); w = build cell id (int bits)
+  int *gid;                // caller's particle id
+};
+
+// Shared (not double-buffered) work arrays of one system.
+struct Work {
+  uint32_t *nbr;           // [npad/32][maxnb][32] neighbour entries
+  int *ncount;             // [n]
+  int *cell_start;         // [ncell + 1]
+  int *bond_e;             // [n][maxb] bond entries of sorted slots (-1: none)
+  int *bond_gid;           // [n][maxb] bond partners by particle id (-1: none)
+  int *rank;               // [n] sorted slot of each particle id
+  double *X;               // [3n] FP64 wrapped positions, pre-sort order
+  double *Xs;              // [3n] FP64 wrapped positions, sorted order
+  uint32_t *key[2], *val[2];  // radix-sort ping-pong buffers
+  uint32_t *hist;          // radix-sort digit counts
+  long long *acc_prof;     // [2*nbins] per-step fixed-point vx sums and counts
+  double *sum_prof;        // [nbins] running vx sums
+  long long *cnt_prof;     // [nbins] running counts
+};
+
+template <class R>
+__device__ __forceinline__ Bufs<R> pick(int cur, const Bufs<R> &a, const Bufs<R> &b) {
+  Bufs<R> r;
+  r.p = cur ? b.p : a.p;
+  r.plo = cur ? b.plo : a.plo;
+  r.v = cur ? b.v : a.v;
+  r.ft = cur ? b.ft : a.ft;
+  r.fc = cur ? b.fc : a.fc;
+  r.pb = cur ? b.pb : a.pb;
+  r.gid = cur ? b.gid : a.gid;
+  return r;
+}
+
+// Image offset of Eq. 4 at integer step n, in [0, Lx).
+__device__ __forceinline__ double image_offset(const Geom &g, long long n) {
+  double t = (double)n * g.dt;
+  double d = fmod(g.shear_rate * g.L[2] * t, g.L[0]);
+  if (d < 0.0) d += g.L[0];
+  return d;
+}
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor bijection; the two key words advance by the Weyl constants
+// (golden ratio and sqrt(3) - 1, scaled to 2^64) between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0;
+    uint64_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Three uniforms on [-1/2, 1/2) for particle `gid` at step `n`, key
+// (seed, system), counter (n, gid, 0, 0).  FP64: the top 53 bits of each word;
+// FP32: the top 24 bits (both conversions are exact).
+template <class R>
+__device__ __forceinline__ void uniform3(const Geom &g, long long n, int gid, R u[3]) {
+  uint64_t c[4] = {(uint64_t)n, (uint64_t)(uint32_t)gid, 0ull, 0ull};
+  philox4x64_10(c, g.seed, g.system);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if constexpr (sizeof(R) == 8)
+      u[k] = (double)(c[k] >> 11) * 0x1.0p-53 - 0.5;
+    else
+      u[k] = (float)(uint32_t)(c[k] >> 40) * 0x1.0p-24f - 0.5f;
+  }
+}
+
+}  // namespace le

@@ -1,0 +1,55 @@
+// Host-side launchers of the LE kernels (implemented in le_kernels.cu and
+// le_sort.cu) and the device-side description of one system.
+#pragma once
+
+#include "le_common.cuh"
+
+namespace le {
+
+constexpr int kDriftThreads = 256;
+constexpr int kForceThreads = 256;
+constexpr int kListThreads = 128;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;   // keys per thread and sort tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortRadixBits = 8;
+constexpr int kSortBuckets = 1 << kSortRadixBits;
+
+struct SysDev {
+  Geom g;
+  Dyn *dyn = nullptr;
+  Bufs<float> f32[2];
+  Bufs<double> f64[2];
+  Work w;
+  int prec = 0;         // 0: FP64, 1: FP32
+  int sort_passes = 1;  // radix passes; the sorted keys end in buffer (sort_passes & 1)
+  int sort_blocks = 1;
+  double *stage = nullptr;   // [6n] host<->device staging (caller order)
+  double *partials = nullptr;// [observe blocks][16]
+};
+
+inline int blocks_for(int n, int threads) { return (n + threads - 1) / threads; }
+
+void launch_drift(const SysDev &s, cudaStream_t st);
+void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, cudaStream_t st);
+// Rebuild pipeline.  from_import: positions come from the import staging
+// (launch_import already binned them); otherwise the current state is re-based.
+void launch_rebuild(const SysDev &s, bool from_import, cudaStream_t st);
+// Re-creates the slot tables, the neighbour list and the bond entries of the
+// current set from its stored build record (checkpoint restore, rollback).
+void launch_relist(const SysDev &s, cudaStream_t st);
+// mode 0: a normal step (forces, thermostat, second half kick, samples);
+// mode 1: initial forces only (velocity unchanged, no samples).
+void launch_force(const SysDev &s, int mode, cudaStream_t st);
+void launch_fold(const SysDev &s, cudaStream_t st);
+void launch_import(const SysDev &s, cudaStream_t st);     // reads stage[0:3n] pos, [3n:6n] vel
+void launch_export(const SysDev &s, cudaStream_t st);     // writes stage: pos, vel; and fc into partial-free area
+void launch_export_forces(const SysDev &s, cudaStream_t st);  // writes stage[0:3n] = Fc
+int observe_blocks(const SysDev &s);
+void launch_observe(const SysDev &s, cudaStream_t st);    // partials[b][0:9] stress sums, [9] epot
+void launch_tables(const SysDev &s, cudaStream_t st);  // slot tables from dyn->s and dyn->f_build
+
+void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, int n, int passes,
+                      int blocks, cudaStream_t st);
+
+}  // namespace le

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances.  FP64 mode: the benchmark spec's bounds, per-step forces within a
+relative 1e-5 (global L2 and per particle against max(|F_i|, <|F|>)) and
+10-step positions within 1e-4.  FP32 mode: forces from FP32 cell-relative
+coordinates; the bound FP32_FORCE_TOL below follows from the rounding of the
+coordinates (see the design notes): per pair the separation carries an error
+of a few units of 2^-24 times the cell edge, which the r^-13 slope of LJ
+multiplies by ~14, and a particle sums ~12 close pairs of force ~30 against a
+net force of ~13.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import force_errors, le_delta
+
+le = pytest.importorskip("paper_2109_11083_gb300")
+
+pytestmark = pytest.mark.gpu
+
+FP64_FORCE_TOL = 1e-5
+FP32_FORCE_TOL_GLOBAL = 2e-5
+FP32_FORCE_TOL_PARTICLE = 2e-4
+POS_TOL = 1e-4
+
+
+def lj_inputs(n, rho, gd, seed, kT=1.0, jitter=0.0):
+    pos, box = synth.lj_box(n, rho, seed)
+    if jitter:
+        pos = np.mod(pos + np.random.default_rng(seed).uniform(-jitter, jitter, pos.shape), box)
+    vel = synth.mb_velocities(n, kT, seed)
+    vel[:, 0] += gd * (pos[:, 2] - 0.5 * box)
+    return pos, vel, box
+
+
+def make_pair(pos, vel, box, gd, rc=2.5, skin=0.3, prec=0, bonds=None, seed=1, xi=1.0, kT=1.0,
+              dt=0.005, thermostat=1, fene_k=30.0, nbins=20, sample_every=1):
+    sim = le.Sim(box, gd, rc, skin, dt=dt, xi=xi, kT=kT, seed=seed, precision=prec,
+                 thermostat=thermostat, fene_k=fene_k, profile_bins=nbins,
+                 sample_every=sample_every)
+    if bonds is not None:
+        sim.set_bonds(bonds)
+    sim.set_particles(pos, vel)
+    p = oracle.params(box, gd, rc, dt=dt, xi=xi, kT=kT, seed=seed, thermostat=thermostat,
+                      fene_k=fene_k if bonds is not None else 0.0, nbins=nbins)
+    ora = oracle.State(p, pos, vel, bonds=bonds)
+    return sim, ora, p
+
+
+def assert_forces(f, ref, prec, what=""):
+    g, q = force_errors(f, ref)
+    if prec == 0:
+        assert g <= FP64_FORCE_TOL and q <= FP64_FORCE_TOL, (what, g, q)
+    else:
+        assert g <= FP32_FORCE_TOL_GLOBAL and q <= FP32_FORCE_TOL_PARTICLE, (what, g, q)
+    return g, q
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_initial_forces_match_oracle(prec):
+    pos, vel, box = lj_inputs(4000, 0.8442, 0.1, 3, jitter=0.1)
+    sim, ora, _ = make_pair(pos, vel, box, 0.1, prec=prec)
+    assert_forces(sim.forces(), ora.Fc, prec, "initial")
+    # total force of Eq. 5 includes the same random numbers on both sides
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forces_every_step_at_high_shear_match_oracle_at_gpu_positions(prec):
+    """High shear so the image offset sweeps the whole box and the lists are
+    rebuilt many times by the image-shift term; at every step the GPU forces
+    equal the oracle's forces evaluated at the GPU's own positions."""
+    gd = 1.0
+    pos, vel, box = lj_inputs(2048, 0.8442, gd, 11)
+    sim, _, p = make_pair(pos, vel, box, gd, prec=prec)
+    worst = (0.0, 0.0)
+    for step in range(1, 241):
+        sim.step(1)
+        r, _ = sim.positions()
+        c = sim.counters()
+        assert c["step"] == step
+        dX = oracle.dX(p, step)
+        assert c["dX"] == dX
+        st, F, _, _ = oracle.forces(p, dX, r)
+        g, q = assert_forces(sim.forces(), F, prec, f"step {step}")
+        worst = (max(worst[0], g), max(worst[1], q))
+    c = sim.counters()
+    assert c["rebuilds"] >= 30 and c["image_rebuilds"] > 0
+    assert dX > 0 and gd * box * 240 * 0.005 > box      # the offset wrapped at least once
+    print(f"prec={prec} worst force errors {worst}, rebuilds {c['rebuilds']} "
+          f"(image-forced {c['image_rebuilds']})")
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_trajectory_parity_lj_fluid_4000(prec):
+    """The FP64 LJ-fluid workload (fcc 4000, rho 0.8442, shear 0.1, Langevin
+    xi = 1 on peculiar velocities): per-step forces and 10-step positions."""
+    w = synth.lj_fluid_4000()
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    sim, ora, p = make_pair(pos, vel, w.box, w.shear_rate, rc=w.rc, skin=w.skin, prec=prec,
+                            seed=w.seed, xi=w.xi, dt=w.dt)
+    for step in range(1, 11):
+        sim.step(1)
+        assert ora.run(1) == oracle.OK
+        assert_forces(sim.forces(), ora.Fc, prec, f"step {step}")
+    r, v = sim.positions()
+    d = le_delta(r, ora.pos, w.box, oracle.dX(p, 10))
+    assert np.abs(d).max() <= POS_TOL
+    assert np.abs(v - ora.vel).max() <= (1e-9 if prec == 0 else 1e-4)
+    sim.close()
+
+
+def test_observables_match_oracle_fp64():
+    """Eq. 15 stress (instantaneous tensor and running xz mean), the vx(z)
+    profile and the peculiar temperature over 200 sampled steps."""
+    gd = 0.5
+    pos, vel, box = lj_inputs(2048, 0.8442, gd, 21)
+    sim, ora, p = make_pair(pos, vel, box, gd, nbins=10)
+    sim.step(200)
+    assert ora.run(200, sample_every=1) == oracle.OK
+    S, xz, ns = sim.stress()
+    S_ref, t_ref, _ = ora.observe()
+    assert ns == 200 == ora.samples.nsamples
+    assert np.abs(S - S_ref).max() <= 1e-8 * np.abs(S_ref).max()
+    assert xz == pytest.approx(ora.samples.sxz_sum / 200, rel=1e-7, abs=1e-9)
+    vx, cnt = sim.velocity_profile()
+    assert np.array_equal(cnt, ora.count)
+    assert np.abs(vx - ora.profile).max() <= 1e-5
+    assert sim.temperature() > 0.5
+    sim.close()
+
+
+def test_checkpoint_restore_is_bitwise():
+    gd = 0.3
+    pos, vel, box = lj_inputs(3000, 0.8442, gd, 5)
+    a = le.Sim(box, gd, 2.5, 0.3, seed=3, precision=1)
+    a.set_particles(pos, vel)
+    a.step(37)
+    blob = a.get_state()
+    a.step(41)
+    ra, va = a.positions()
+    fa = a.forces()
+    b = le.Sim(box, gd, 2.5, 0.3, seed=3, precision=1)
+    b.set_particles(pos, vel)
+    b.set_state(blob)
+    b.step(41)
+    rb, vb = b.positions()
+    assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+    assert np.array_equal(fa, b.forces())
+    assert a.counters()["step"] == b.counters()["step"] == 78
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kremer_grest_chains_fene_parity(prec):
+    """WCA (Eq. 10 at rc = 2^(1/6)) + FENE (Eq. 11) chains under strong shear:
+    forces at every step against the oracle at the GPU's positions."""
+    pos, box, bonds = synth.lattice_chains(40, 25, 0.85, 13)
+    gd = 0.5
+    vel = synth.mb_velocities(pos.shape[0], 1.0, 13)
+    vel[:, 0] += gd * (pos[:, 2] - 0.5 * box)
+    rc = 2 ** (1 / 6)
+    sim, ora, p = make_pair(pos, vel, box, gd, rc=rc, skin=0.3, prec=prec, bonds=bonds,
+                            dt=0.005, xi=0.5)
+    assert_forces(sim.forces(), ora.Fc, prec, "initial")
+    for step in range(1, 151):
+        sim.step(1)
+        if step % 5:
+            continue
+        r, _ = sim.positions()
+        st, F, _, _ = oracle.forces(p, oracle.dX(p, step), r, bonds)
+        assert st == oracle.OK
+        assert_forces(sim.forces(), F, prec, f"step {step}")
+    sim.close()
+
+
+def test_broken_bond_is_reported_and_rolled_back():
+    pos = np.array([[2.0, 2.0, 2.0], [3.0, 2.0, 2.0], [5.0, 5.0, 5.0]])
+    vel = np.array([[-30.0, 0, 0], [30.0, 0, 0], [0, 0, 0]])
+    sim = le.Sim(10.0, 0.0, 2 ** (1 / 6), 0.3, thermostat=0, dt=0.01)
+    sim.set_bonds([[0, 1]])
+    sim.set_particles(pos, vel)
+    r0, v0 = sim.positions()
+    with pytest.raises(le.LEError) as e:
+        sim.step(50)
+    assert e.value.status == 5
+    r1, v1 = sim.positions()
+    assert np.array_equal(r0, r1) and np.array_equal(v0, v1)
+    assert sim.counters()["step"] == 0
+    sim.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 257])
+def test_tiny_and_ragged_systems(n):
+    """Sizes that fill no warp or block evenly; one particle is a free particle
+    on the sheared image lattice."""
+    gd = 0.7
+    box = np.array([9.0, 8.0, 7.5])
+    g = np.random.default_rng(n)
+    pos = g.uniform(0, 1, (n, 3)) * box
+    if n > 1:  # keep the random gas free of overlaps
+        pos, _ = synth.lj_box(n, n / float(np.prod(box)), n)
+        pos = pos * (box / pos.max(axis=0).clip(1e-9)) * 0.999
+    vel = g.normal(size=(n, 3))
+    sim, ora, p = make_pair(pos, vel, box, gd, thermostat=0, prec=0)
+    for _ in range(5):
+        sim.step(20)
+        assert ora.run(20) == oracle.OK
+    r, v = sim.positions()
+    d = le_delta(r, ora.pos, box, oracle.dX(p, 100))
+    assert np.abs(d).max() <= 1e-9
+    assert np.abs(v - ora.vel).max() <= 1e-9
+    sim.close()
+
+
+def test_two_cells_per_dimension_small_box():
+    """N = 500 at rho = 0.9: L = 8.22 gives only 2 cells of edge >= 2.8, so a
+    neighbour cell is reached through two different images."""
+    gd = 0.2
+    pos, vel, box = lj_inputs(500, 0.9, gd, 17)
+    sim, _, p = make_pair(pos, vel, box, gd, prec=1)
+    assert sim.counters()["cells"] == (2, 2, 2)
+    for step in range(1, 101):
+        sim.step(1)
+        if step % 10 == 0:
+            r, _ = sim.positions()
+            _, F, _, _ = oracle.forces(p, oracle.dX(p, step), r, use_cells=False)
+            assert_forces(sim.forces(), F, 1, f"step {step}")
+    sim.close()
+
+
+def test_negative_shear_and_zero_shear():
+    for gd in (-0.8, 0.0):
+        pos, vel, box = lj_inputs(1372, 0.8442, gd, 31)
+        sim, ora, p = make_pair(pos, vel, box, gd, prec=0)
+        sim.step(60)
+        assert ora.run(60) == oracle.OK
+        assert_forces(sim.forces(), ora.Fc, 0, f"shear {gd}")
+        sim.close()
+
+
+def test_full_size_box_sampled_forces():
+    """The 4,194,304-particle box in the benchmark's launch configuration:
+    after a few steps, forces on 3000 sampled particles against the oracle's
+    one-particle-at-a-time sums."""
+    w = synth.lj_box_4m()
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    sim = le.Sim(w.box, w.shear_rate, w.rc, w.skin, dt=w.dt, xi=w.xi, seed=w.seed, precision=1)
+    sim.set_particles(pos, vel)
+    sim.step(12)
+    r, _ = sim.positions()
+    f = sim.forces()
+    p = oracle.params(w.box, w.shear_rate, w.rc)
+    idx = np.random.default_rng(0).choice(w.n, 3000, replace=False)
+    F = oracle.forces_on(p, oracle.dX(p, 12), r, idx)
+    g, q = force_errors(f[idx], F)
+    assert g <= FP32_FORCE_TOL_GLOBAL and q <= FP32_FORCE_TOL_PARTICLE, (g, q)
+    assert sim.counters()["rebuilds"] >= 1
+    sim.close()
