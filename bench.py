@@ -1,0 +1,328 @@
+"""Benchmark of the Lees-Edwards shear-flow MD step on GB300.
+
+One benchmark step is one MD step of the whole hot path (kick/drift, the
+rebuild trigger and, when it fires, resort + LE-aware Verlet list, pair forces
+with the peculiar-velocity Langevin thermostat, stress and profile sums) on the
+large single LJ box: N = 4,194,304 particles, density 0.8442, rc = 2.5,
+skin 0.3, shear rate 0.05, dt 0.005, Langevin xi = 1, FP32 forces with
+FP64-class positions.  Inputs are resident in HBM when the timed region starts
+(the state touched per step, ~1.9 GB, is far larger than the 129 MB L2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-steps/s"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--particles", type=int, default=4194304,
+                    help="box size (the default is the benchmark workload; smaller boxes "
+                         "of the same density are for profiler captures)")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(w):
+    return {"workload": w.name, "n_particles": w.n, "density": w.rho, "box": round(w.box, 6),
+            "rc": w.rc, "skin": w.skin, "shear_rate": w.shear_rate, "dt": w.dt,
+            "langevin_xi": w.xi, "kT": w.kT, "thermostat": "peculiar",
+            "l2_policy": "inputs larger than L2 (state touched per step ~1.9 GB >> 129 MB)"}
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_rate(n_sample: int, target_s: float, max_steps: int | None = None):
+    """The CPU oracle, as it stands, on an n_sample-particle sub-box of the
+    same LJ workload: (particle-steps/s, steps, seconds)."""
+    import oracle
+    base = synth.lj_box_4m()
+    w = synth.scaled_lj(base, n_sample)
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    p = oracle.params(w.box, w.shear_rate, w.rc, dt=w.dt, xi=w.xi, kT=w.kT, seed=w.seed)
+    s = oracle.State(p, pos, vel)
+    t0 = time.perf_counter()
+    s.run(1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(max_steps or 10 ** 9, int(target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    s.run(steps)
+    dt = time.perf_counter() - t0
+    return n_sample * steps / dt, steps, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    base = synth.lj_box_4m()
+    # each timed step is one oracle step of a 16,384-particle sub-box (about
+    # 0.1 s on one core), so --steps K finishes in roughly K/10 seconds
+    n_sample = 16384
+    import oracle
+    w = synth.scaled_lj(base, n_sample)
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    p = oracle.params(w.box, w.shear_rate, w.rc, dt=w.dt, xi=w.xi, kT=w.kT, seed=w.seed)
+    s = oracle.State(p, pos, vel)
+    s.run(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    s.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = n_sample * args.steps / dt
+    sample = (f"{n_sample}-particle sub-box of the same LJ workload (fcc, density 0.8442, "
+              f"rc 2.5, skin unused, shear 0.05, dt 0.005, xi 1), one oracle step per "
+              f"benchmark step, cell-list FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(base),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="le_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def force_kernel_bytes(n: int, mean_nb: float) -> float:
+    """Algorithmic HBM bytes of one pair-force launch (FP32 mode): per
+    particle own position 16 + list count 4 + 4 per list entry + half-step
+    velocity 16 + particle id 4 (random-force counter), writes conservative
+    force 16 + total force 16 + velocity 16.  Neighbour positions are gathered
+    from cache (counted once in the own-position read)."""
+    return n * (16 + 4 + 4 * mean_nb + 16 + 4 + 16 + 16 + 16)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel_file: str):
+    """Per-particle DRAM bytes of the pair-force kernel from the committed ncu
+    summary, if it was taken on the current source."""
+    import hashlib
+    summary = os.path.join(ROOT, "profiles", "k_force_lj_box_n4194304.md")
+    if not os.path.exists(summary):
+        return None
+    sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(summary):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_particle"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    import paper_2109_11083_gb300 as le
+
+    w = synth.lj_box_4m()
+    if args.particles != w.n:
+        w = synth.scaled_lj(w, args.particles, f"lj_box_n{args.particles}_fp32")
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    stream = torch.cuda.current_stream()
+    sim = le.Sim(w.box, w.shear_rate, w.rc, w.skin, stream=stream, dt=w.dt, xi=w.xi, kT=w.kT,
+                 seed=w.seed, system_id=rank, precision=le.LE_FP32, sample_every=1,
+                 profile_bins=20)
+    sim.set_particles(pos, vel)
+    sim.step(args.warmup)
+    c0 = sim.counters()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler take its first reading under load
+    force_ms, drift_ms, total_ms = sim.step_profiled(args.steps)
+    barrier()
+    clk = clocks.stop()
+    c1 = sim.counters()
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = w.n * world * args.steps / (max_ms * 1e-3)
+
+    rebuilds = c1["rebuilds"] - c0["rebuilds"]
+    passes = math.ceil(max(1, math.ceil(math.log2(max(2, c1["cells"][0] * c1["cells"][1] *
+                                                        c1["cells"][2])))) / 8)
+    launches = 3 * args.steps + rebuilds * (1 + 3 * passes + 4)
+    mean_nb = c1["list_mean"]
+    kbytes = force_kernel_bytes(w.n, mean_nb)
+    f_avg_s = force_ms / args.steps * 1e-3
+    achieved = kbytes / f_avg_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic_pp = profiled_traffic(os.path.join(ROOT, "paper_2109_11083_gb300", "csrc",
+                                               "le_kernels.cu"))
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            rate, steps, secs = oracle_rate(131072, 12.0)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"131072-particle sub-box of the same LJ workload, {steps} oracle "
+                             f"steps ({secs:.1f} s, FP64, cell list, one thread)"}
+        e2e = None
+        if not args.no_e2e:
+            import torch as _t
+            hp = _t.from_numpy(pos).pin_memory().numpy()
+            hv = _t.from_numpy(vel).pin_memory().numpy()
+            out_p = _t.empty((w.n, 3), dtype=_t.float64).pin_memory().numpy()
+            out_v = _t.empty((w.n, 3), dtype=_t.float64).pin_memory().numpy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.set_particles(hp, hv)
+            sim.step(args.steps)
+            le.le_positions(sim.h, w.n, out_p, out_v)
+            sim.stress(instantaneous=False)
+            sim.velocity_profile()
+            torch.cuda.synchronize()
+            e_s = time.perf_counter() - t0
+            e2e = {"value": w.n * args.steps / e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": 48 * w.n / args.steps,
+                   "d2h_bytes_per_step": (48 * w.n + 8 * 3 + 16 * 20) / args.steps,
+                   "what": "le_set_particles (host pinned pos/vel, initial list and forces) + "
+                           "le_step(K) + le_positions + le_stress + le_velocity_profile"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(w), parallelism="replicas" if world > 1 else "single"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "k_force (pair force + Langevin + kick + samples)",
+                         "algorithmic_bytes_per_launch": kbytes,
+                         "avg_launch_ms": f_avg_s * 1e3,
+                         "traffic": (traffic_pp * w.n if traffic_pp else None)},
+            "kernel_ms_per_step": {"k_force": force_ms / args.steps,
+                                   "k_drift": drift_ms / args.steps,
+                                   "rest": (total_ms - force_ms - drift_ms) / args.steps},
+            "rebuilds": rebuilds, "image_rebuilds": c1["image_rebuilds"] - c0["image_rebuilds"],
+            "mean_list_length": mean_nb,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

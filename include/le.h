@@ -162,6 +162,7 @@ typedef struct le_counters {
     int64_t list_max;         /* largest neighbour count seen at a rebuild */
     int64_t cells[3];         /* cell grid */
     double  dX;               /* current image offset */
+    double  list_mean;        /* mean neighbour count of the last build */
 } le_counters;
 
 LE_API le_status le_get_counters(le_sim *s, le_counters *out);

@@ -108,6 +108,9 @@ def lib():
             L.ora_forces_on.restype = None
             L.ora_forces_on.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
                                         C.c_int64, C.POINTER(C.c_int64), _D]
+            L.ora_force_error_bound.restype = None
+            L.ora_force_error_bound.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
+                                                C.c_int64, _I32, C.c_double, C.c_double, _D]
             L.ora_observe.restype = C.c_int
             L.ora_observe.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, _D, _D,
                                       C.c_int64, _I32, C.c_int, _D, _D, _D]
@@ -188,6 +191,18 @@ def forces_on(p: Params, dx_offset: float, pos, idx) -> np.ndarray:
     lib().ora_forces_on(C.byref(p), dx_offset, pos.shape[0], _dp(pos), ii.size,
                         ii.ctypes.data_as(C.POINTER(C.c_int64)), _dp(F))
     return F
+
+
+def force_error_bound(p: Params, dx_offset: float, pos, bonds=None, u: float = 2.0 ** -24,
+                      P: float = 1.6) -> np.ndarray:
+    """Per-particle first-order bound on the error of forces computed with
+    unit roundoff u from reference-relative coordinates (|p| <= P)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    b = _bonds(bonds)
+    B = np.zeros(pos.shape[0])
+    lib().ora_force_error_bound(C.byref(p), dx_offset, pos.shape[0], _dp(pos), b.shape[0],
+                                b.ctypes.data_as(_I32), u, P, _dp(B))
+    return B
 
 
 class State:

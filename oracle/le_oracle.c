@@ -357,6 +357,77 @@ void ora_forces_on(const ora_params *p, double dX, int64_t n, const double *pos,
     if (cells) grid_free(&g);
 }
 
+/* First-order bound on the error of a force computed in a floating-point
+ * format of unit roundoff u from coordinates stored relative to reference
+ * points no farther than P (per component) from the particle:
+ *   - each separation component carries an error of at most u*(6P + 2r)
+ *     (two rounded coordinates, one rounded offset between references,
+ *     two additions);
+ *   - a pair force F = f(r) d then moves by at most J(r)*sqrt(3)*u*(6P + 2r)
+ *     with J = |f| + r|f'| (the norm of dF/dd);
+ *   - its evaluation adds 16u|F| and a sequential sum of m terms adds
+ *     (m + 2)u * sum |F_ij|.
+ * B[i] receives the bound for particle i (LJ of Eq. 9 and FENE of Eq. 11).
+ * Test infrastructure: used only to set the tolerance of reduced-precision
+ * comparisons. */
+typedef struct {
+    const ora_params *p;
+    double dX, u, P;
+    const double *pos;
+    double *B, *S;
+    int64_t *m;
+} bound_ctx;
+
+static void bound_add(bound_ctx *c, int64_t i, double r2, double f, double rfp)
+{
+    double r = sqrt(r2);
+    double J = fabs(f) + fabs(rfp);
+    c->B[i] += J * sqrt(3.0) * c->u * (6.0 * c->P + 2.0 * r) + 16.0 * c->u * fabs(f) * r;
+    c->S[i] += fabs(f) * r;
+    c->m[i] += 1;
+}
+
+static void bound_visit(void *vctx, int64_t i, int64_t j)
+{
+    bound_ctx *c = (bound_ctx *)vctx;
+    double d[3];
+    ora_min_image(c->p, c->dX, c->pos + 3 * i, c->pos + 3 * j, d);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < c->p->rc * c->p->rc)) return;
+    double e, f = lj_f_over_r(c->p, r2, &e);
+    double s2 = c->p->sigma * c->p->sigma / r2, s6 = s2 * s2 * s2;
+    /* r f'(r) for f = 24 eps (2 s^12 r^-2 - s^6 r^-2) */
+    double rfp = 24.0 * c->p->eps * (-28.0 * s6 * s6 + 8.0 * s6) / r2;
+    bound_add(c, i, r2, f, rfp);
+}
+
+void ora_force_error_bound(const ora_params *p, double dX, int64_t n, const double *pos,
+                           int64_t nbond, const int32_t *bonds, double u, double P,
+                           double *B)
+{
+    bound_ctx c;
+    c.p = p; c.dX = dX; c.u = u; c.P = P; c.pos = pos; c.B = B;
+    c.S = (double *)calloc((size_t)n, sizeof(double));
+    c.m = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    memset(B, 0, sizeof(double) * n);
+    if (p->eps != 0.0) for_candidates(p, n, pos, 1, &c, bound_visit);
+    double R02 = p->fene_R0 * p->fene_R0;
+    for (int64_t b = 0; b < nbond; ++b) {
+        int64_t ends[2] = {bonds[2 * b], bonds[2 * b + 1]};
+        double d[3];
+        ora_min_image(p, dX, pos + 3 * ends[0], pos + 3 * ends[1], d);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double x = 1.0 - r2 / R02;
+        if (!(x > 0.0)) continue;
+        double f = -p->fene_k / x;
+        double rfp = -2.0 * p->fene_k * r2 / (R02 * x * x);
+        for (int q = 0; q < 2; ++q) bound_add(&c, ends[q], r2, f, rfp);
+    }
+    for (int64_t i = 0; i < n; ++i) B[i] += (double)(c.m[i] + 2) * u * c.S[i];
+    free(c.S);
+    free(c.m);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Eq. 5: total force = conservative - xi*m*(v - v_s(z) e_x) + random, the
  * friction acting on the peculiar velocity.  v is the half-step velocity. */

@@ -56,6 +56,7 @@ class le_counters(C.Structure):
         ("step", C.c_int64), ("particles", C.c_int64), ("rebuilds", C.c_int64),
         ("image_rebuilds", C.c_int64), ("list_capacity", C.c_int64),
         ("list_max", C.c_int64), ("cells", C.c_int64 * 3), ("dX", C.c_double),
+        ("list_mean", C.c_double),
     ]
 
 
@@ -227,7 +228,7 @@ def le_get_counters(h: int) -> dict:
     _check(h, lib().le_get_counters(h, C.byref(c)))
     return dict(step=c.step, particles=c.particles, rebuilds=c.rebuilds,
                 image_rebuilds=c.image_rebuilds, list_capacity=c.list_capacity,
-                list_max=c.list_max, cells=tuple(c.cells), dX=c.dX)
+                list_max=c.list_max, cells=tuple(c.cells), dX=c.dX, list_mean=c.list_mean)
 
 
 def le_get_state(h: int) -> bytes:

@@ -704,6 +704,7 @@ LE_API le_status le_get_counters(le_sim *s, le_counters *out) {
   out->list_max = s->h_dyn->list_max;
   for (int a = 0; a < 3; ++a) out->cells[a] = s->s.g.nc[a];
   out->dX = s->h_dyn->dX;
+  out->list_mean = (double)s->h_dyn->list_entries / (double)s->n;
   return LE_OK;
 }
 

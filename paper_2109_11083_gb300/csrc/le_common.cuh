@@ -33,6 +33,8 @@ namespace le {
 constexpr int kIndexBits = 25;
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int kNumSlots = 90;
+// end marker of a particle's bond entries (slot 127 is never a valid code)
+constexpr uint32_t kNoBond = 0xFFFFFFFFu;
 constexpr int kMaxBonds = 8;
 constexpr int kMaxBins = 1024;
 constexpr int64_t kMaxParticles = int64_t(1) << kIndexBits;
@@ -99,6 +101,7 @@ struct Dyn {
   int force_rebuild;     // set by the host to force the next step to rebuild
   int pending;           // per-step accumulators hold an unfolded sample
   long long nrebuild, nimage;
+  long long list_entries;        // neighbour entries written by the last build
   long long acc_sxz, acc_ke;     // per-step fixed-point sums (see kFix)
   double sum_sxz, sum_tpec;      // running sums over samples
   long long nsamples;
@@ -130,7 +133,7 @@ struct Work {
   uint32_t *nbr;           // [npad/32][maxnb][32] neighbour entries
   int *ncount;             // [n]
   int *cell_start;         // [ncell + 1]
-  int *bond_e;             // [n][maxb] bond entries of sorted slots (-1: none)
+  uint32_t *bond_e;        // [n][maxb] bond entries of sorted slots (kNoBond: none)
   int *bond_gid;           // [n][maxb] bond partners by particle id (-1: none)
   int *rank;               // [n] sorted slot of each particle id
   double *X;               // [3n] FP64 wrapped positions, pre-sort order

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
       d->f_build = f;
       d->dX_build = dX1;
       d->build_step = n1;
+      d->list_entries = 0;
       d->nrebuild += 1;
       if (!disp_need && !d->force_rebuild) d->nimage += 1;
       s = f;
@@ -328,11 +329,11 @@ __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict
     if constexpr (BONDS) {
       const R R02 = R(g.fene_R0 * g.fene_R0), kf = R(g.fene_k);
       for (int q = 0; q < g.maxb; ++q) {
-        const int e = w.bond_e[(size_t)i * g.maxb + q];
-        if (e < 0) break;
-        const int j = e & (int)kIndexMask;
+        const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
+        if (e == kNoBond) break;
+        const int j = (int)(e & kIndexMask);
         const V4<R> pj = load4(b.p + j);
-        const V4<R> o = s_off[(uint32_t)e >> kIndexBits];
+        const V4<R> o = s_off[e >> kIndexBits];
         const R dx = (pi.x - pj.x) + o.x;
         const R dy = (pi.y - pj.y) + o.y;
         const R dz = (pi.z - pj.z) + o.z;
@@ -557,6 +558,7 @@ __global__ void k_relist_prep(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s
 // Slot-offset tables from d->s (this step) and d->f_build (last build).
 __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
   const double s = d->s, fb = d->f_build;
+  if (threadIdx.x == 0) d->list_entries = 0;
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) {
     int k, dcy, dcz, cross;
     slot_decode(e, k, dcy, dcz, cross);
@@ -585,7 +587,8 @@ __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restric
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
+  int cnt = 0;
+  if (i < g.n) {
   const float4 qi = b.pb[i];
   int cx, cy, cz;
   cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
@@ -595,7 +598,6 @@ __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restric
   const double rho = g.rl / g.lc[0] * (1.0 + 1e-5) + 1e-9;
   const int mb = d->m_build;
   uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
-  int cnt = 0;
   for (int dcz = -1; dcz <= 1; ++dcz) {
     int czj = cz - dcz, cross = 0;
     if (czj < 0) { czj += g.nc[2]; cross = 1; }
@@ -641,6 +643,17 @@ __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restric
   w.ncount[i] = cnt;
   atomicMax(&d->list_max, cnt);
   if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
+  }
+  // total list entries (for the mean list length), one atomic per block
+  __shared__ unsigned long long s_tot[kListThreads / 32];
+  const unsigned long long c = warp_sum((unsigned long long)cnt);
+  if ((threadIdx.x & 31) == 0) s_tot[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < kListThreads / 32; ++k) t += s_tot[k];
+    atomicAdd((unsigned long long *)&d->list_entries, t);
+  }
 }
 
 // ------------------------------------------------------------ rebuild: bonds
@@ -660,7 +673,7 @@ __global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, B
   cell_coords(g, __float_as_int(b.pb[k].w), ck[0], ck[1], ck[2]);
   for (int q = 0; q < g.maxb; ++q) {
     const int h = w.bond_gid[(size_t)gid * g.maxb + q];
-    int entry = -1;
+    uint32_t entry = kNoBond;
     if (h >= 0 && h < g.n) {
       const int j = min(max(w.rank[h], 0), g.n - 1);
       const double *xi = w.Xs + 3 * (size_t)k;
@@ -687,7 +700,7 @@ __global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, B
           (cross && dcz == 0)) {
         atomicOr(&d->err, (int)kErrSlot);
       } else {
-        entry = j | (slot_code(kk, dcy, dcz, cross) << kIndexBits);
+        entry = (uint32_t)j | ((uint32_t)slot_code(kk, dcy, dcz, cross) << kIndexBits);
       }
     }
     w.bond_e[(size_t)k * g.maxb + q] = entry;
@@ -796,9 +809,9 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
     }
     if constexpr (BONDS) {
       for (int q = 0; q < g.maxb; ++q) {
-        const int e = w.bond_e[(size_t)i * g.maxb + q];
-        if (e < 0) break;
-        pair(e & (int)kIndexMask, (int)((uint32_t)e >> kIndexBits), true);
+        const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
+        if (e == kNoBond) break;
+        pair((int)(e & kIndexMask), (int)(e >> kIndexBits), true);
       }
     }
     const V4<R> v = b.v[i];
