@@ -118,7 +118,7 @@ LE_API le_status le_set_bonds(le_sim *s, int64_t nb, const int32_t *pairs);
 /* Loads n particles: pos (n x 3, row-major, any real coordinates; they are
  * wrapped into the box as images at step 0, where dX = 0) and lab-frame vel
  * (n x 3).  Resets the step counter to 0, the samples and the counters, builds
- * the cell/Verlet lists and computes the initial total force.  1 <= n <= 2^25.
+ * the cell/Verlet lists and computes the initial total force.  1 <= n <= 2^24 (16,777,216).
  * Errors: LE_ERR_INVALID_ARG, LE_ERR_OOM, LE_ERR_BOND_BROKEN, LE_ERR_CUDA. */
 LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const double *vel);
 
@@ -183,6 +183,12 @@ LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes);
  * (milliseconds) and the whole graph's device time.  Meant for measurement. */
 LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms,
                                   double *integrate_ms, double *total_ms);
+
+/* eager != 0: launch every kernel directly on the stream instead of through
+ * CUDA graphs; the host reads the rebuild decision back after each step.
+ * The kernels and the results are identical.  Profilers that cannot look
+ * inside graphs with conditional nodes need this mode; it is slower. */
+LE_API le_status le_set_eager(le_sim *s, int eager);
 
 LE_API le_status le_destroy(le_sim *s);
 LE_API const char *le_last_error(const le_sim *s);

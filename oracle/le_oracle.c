@@ -393,7 +393,17 @@ static void bound_visit(void *vctx, int64_t i, int64_t j)
     double d[3];
     ora_min_image(c->p, c->dX, c->pos + 3 * i, c->pos + 3 * j, d);
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < c->p->rc * c->p->rc)) return;
+    double rc = c->p->rc;
+    /* a pair within the separation error band of the cut-off may fall on
+     * either side of the strict r < rc test: either answer is a correct
+     * reduced-precision result, so the bound admits the whole pair force */
+    double band = sqrt(3.0) * c->u * (6.0 * c->P + 2.0 * rc);
+    double r = sqrt(r2);
+    if (fabs(r - rc) <= band) {
+        double ec, fc = lj_f_over_r(c->p, rc * rc, &ec);
+        c->B[i] += fabs(fc) * rc;
+    }
+    if (!(r2 < rc * rc)) return;
     double e, f = lj_f_over_r(c->p, r2, &e);
     double s2 = c->p->sigma * c->p->sigma / r2, s6 = s2 * s2 * s2;
     /* r f'(r) for f = 24 eps (2 s^12 r^-2 - s^6 r^-2) */
@@ -410,7 +420,11 @@ void ora_force_error_bound(const ora_params *p, double dX, int64_t n, const doub
     c.S = (double *)calloc((size_t)n, sizeof(double));
     c.m = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     memset(B, 0, sizeof(double) * n);
-    if (p->eps != 0.0) for_candidates(p, n, pos, 1, &c, bound_visit);
+    if (p->eps != 0.0) {
+        ora_params q = *p;  /* a grid edge slightly above rc also covers the band */
+        q.rc = p->rc * (1.0 + 1e-4);
+        for_candidates(&q, n, pos, 1, &c, bound_visit);
+    }
     double R02 = p->fene_R0 * p->fene_R0;
     for (int64_t b = 0; b < nbond; ++b) {
         int64_t ends[2] = {bonds[2 * b], bonds[2 * b + 1]};

@@ -98,6 +98,7 @@ def lib():
                 "le_get_counters": (C.c_int, [_P, C.POINTER(le_counters)]),
                 "le_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
                 "le_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+                "le_set_eager": (C.c_int, [_P, C.c_int]),
                 "le_destroy": (C.c_int, [_P]),
                 "le_last_error": (C.c_char_p, [_P]),
                 "le_status_string": (C.c_char_p, [C.c_int]),
@@ -115,7 +116,8 @@ def exported_symbols() -> list[str]:
     return ["le_default_params", "le_create", "le_set_bonds", "le_set_particles", "le_step",
             "le_step_profiled", "le_forces", "le_positions", "le_stress",
             "le_velocity_profile", "le_temperature", "le_reset_samples", "le_get_counters",
-            "le_get_state", "le_set_state", "le_destroy", "le_last_error", "le_status_string"]
+            "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
+            "le_status_string"]
 
 
 def _check(h, st: int):
@@ -244,6 +246,10 @@ def le_set_state(h: int, blob: bytes) -> None:
     _check(h, lib().le_set_state(h, C.cast(buf, _P), len(blob)))
 
 
+def le_set_eager(h: int, eager: bool) -> None:
+    _check(h, lib().le_set_eager(h, 1 if eager else 0))
+
+
 def le_destroy(h: int) -> None:
     _check(None, lib().le_destroy(h))
 
@@ -304,6 +310,9 @@ class Sim:
 
     def set_state(self, blob):
         le_set_state(self.h, blob)
+
+    def set_eager(self, eager=True):
+        le_set_eager(self.h, eager)
 
     def close(self):
         if self.h:

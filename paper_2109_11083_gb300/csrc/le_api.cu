@@ -44,6 +44,7 @@ struct le_sim {
   long long *h_scalar = nullptr;     // pinned host scratch
   Dyn *h_dyn = nullptr;              // pinned mirror of the device record
   cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
+  bool eager = false;                // launch kernels directly (no graphs)
   // rollback snapshot of the current buffer set and the dynamic record
   std::vector<void *> snap;
   std::string err;
@@ -129,6 +130,7 @@ le_status status_from_err(le_sim *s, int err) {
   if (err & kErrNonfinite) return fail(s, LE_ERR_NONFINITE, "a force or velocity became non-finite");
   if (err & kErrCapacity) return fail(s, LE_ERR_CAPACITY, "neighbour list capacity exceeded");
   if (err & kErrSlot) return fail(s, LE_ERR_BOND_BROKEN, "a bond spans more than one cell");
+  if (err & kErrTimeout) return fail(s, LE_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
   return LE_OK;
 }
 
@@ -167,7 +169,8 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   CKS(dalloc(s, &w.bond_e, (size_t)n * mb));
   CKS(dalloc(s, &w.bond_gid, (size_t)n * mb));
   CKS(dalloc(s, &w.rank, n));
-  CKS(dalloc(s, &w.X, 3 * (size_t)n));
+  CKS(dalloc(s, (char **)&w.tmp_p, (size_t)n * vb));
+  if (prec == 1) CKS(dalloc(s, &w.tmp_lo, n));
   CKS(dalloc(s, &w.Xs, 3 * (size_t)n));
   for (int k = 0; k < 2; ++k) {
     CKS(dalloc(s, &w.key[k], n));
@@ -175,6 +178,7 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   }
   s->s.sort_blocks = (int)((n + kSortTile - 1) / kSortTile);
   CKS(dalloc(s, &w.hist, (size_t)kSortBuckets * s->s.sort_blocks));
+  CKS(dalloc(s, &s->s.sort_part, sort_scan_parts(s->s.sort_blocks)));
   CKS(dalloc(s, &w.acc_prof, 2 * (size_t)g.nbins));
   CKS(dalloc(s, &w.sum_prof, (size_t)g.nbins));
   CKS(dalloc(s, &w.cnt_prof, (size_t)g.nbins));
@@ -197,11 +201,15 @@ void choose_cells(le_sim *s) {
     g.nc[a] = std::max(1, (int)std::floor(g.L[a] / edge));
     g.lc[a] = g.L[a] / g.nc[a];
     g.ncell *= g.nc[a];
+    g.inv_lc[a] = (float)(1.0 / g.lc[a]);
+    g.half_lc_f[a] = (float)(0.5 * g.lc[a] * (1.0 + 1e-6) + 1e-6);
+    g.lc_hi[a] = (float)g.lc[a];
+    g.lc_lo[a] = (float)(g.lc[a] - (double)g.lc_hi[a]);
   }
   int bits = 1;
   while ((1ll << bits) < (long long)g.ncell) ++bits;
   g.sort_bits = bits;
-  s->s.sort_passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+  s->s.sort_passes = sort_passes_for(bits);
 }
 
 // ------------------------------------------------------------- graph capture
@@ -217,7 +225,7 @@ le_status capture(le_sim *s, int steps, std::vector<cudaEvent_t> *ev, cudaGraphE
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 0], s->cap_main, cudaEventRecordExternal);
     launch_drift(s->s, s->cap_main);
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 1], s->cap_main, cudaEventRecordExternal);
-    launch_decide(s->s, handles[k], s->cap_main);
+    launch_decide(s->s, handles[k], 1, s->cap_main);
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus cs;
@@ -416,6 +424,42 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
   g.sample_every = p->sample_every;
   g.seed = p->seed;
   g.system = p->system_id;
+  {
+    const double rlb = rl * (1.0 + 1e-5);
+    g.rl2_build = (float)(rlb * rlb);
+    KConst<double> &c = g.cd;
+    c.half_dt_m = 0.5 * p->dt / p->mass;
+    c.dt = p->dt;
+    c.rc2 = rc * rc;
+    c.sig2 = p->sigma * p->sigma;
+    c.eps24 = 24.0 * p->eps;
+    c.amp = std::sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
+    c.xim = p->xi * p->mass;
+    c.shear = shear_rate;
+    c.half_Lz = 0.5 * box[2];
+    c.Lz = box[2];
+    c.shear_Lz = shear_rate * box[2];
+    c.R02 = p->fene_R0 * p->fene_R0;
+    c.fene_k = p->fene_k;
+    c.mass = p->mass;
+    c.bins_per_Lz = p->profile_bins / box[2];
+    KConst<float> &f = g.cf;
+    f.half_dt_m = (float)c.half_dt_m;
+    f.dt = (float)c.dt;
+    f.rc2 = (float)c.rc2;
+    f.sig2 = (float)c.sig2;
+    f.eps24 = (float)c.eps24;
+    f.amp = (float)c.amp;
+    f.xim = (float)c.xim;
+    f.shear = (float)c.shear;
+    f.half_Lz = (float)c.half_Lz;
+    f.Lz = (float)c.Lz;
+    f.shear_Lz = (float)c.shear_Lz;
+    f.R02 = (float)c.R02;
+    f.fene_k = (float)c.fene_k;
+    f.mass = (float)c.mass;
+    f.bins_per_Lz = (float)c.bins_per_Lz;
+  }
   s->s.prec = p->precision;
   cudaError_t e;
   if (cuda_stream) {
@@ -434,6 +478,12 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
     return LE_ERR_CUDA;
   }
   *out = s;
+  return LE_OK;
+}
+
+LE_API le_status le_set_eager(le_sim *s, int eager) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  s->eager = eager != 0;
   return LE_OK;
 }
 
@@ -518,7 +568,30 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
   return fail(s, LE_ERR_CAPACITY, "neighbour list could not be sized");
 }
 
+// One step without graphs: the host reads the rebuild decision back.
+static le_status eager_step(le_sim *s, cudaEvent_t *ev) {
+  if (ev) CK(cudaEventRecord(ev[0], s->stream));
+  launch_drift(s->s, s->stream);
+  if (ev) CK(cudaEventRecord(ev[1], s->stream));
+  launch_decide(s->s, 0, 0, s->stream);
+  CK(cudaMemcpyAsync(s->h_scalar, &s->s.dyn->rebuild, sizeof(int), cudaMemcpyDeviceToHost,
+                     s->stream));
+  CKS(sync(s));
+  if (*(int *)s->h_scalar) launch_rebuild(s->s, false, s->stream);
+  if (ev) CK(cudaEventRecord(ev[2], s->stream));
+  launch_force(s->s, 0, s->stream);
+  if (ev) CK(cudaEventRecord(ev[3], s->stream));
+  CK(cudaGetLastError());
+  return LE_OK;
+}
+
 static le_status step_once(le_sim *s, int64_t nsteps) {
+  if (s->eager) {
+    for (int64_t k = 0; k < nsteps; ++k) CKS(eager_step(s, nullptr));
+    launch_fold(s->s, s->stream);
+    CK(cudaGetLastError());
+    return read_dyn(s);
+  }
   CKS(ensure_graphs(s));
   int64_t left = nsteps;
   while (left >= kChunk) {
@@ -570,13 +643,22 @@ LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms, d
   CK(cudaEventCreate(&t0));
   CK(cudaEventCreate(&t1));
   cudaGraphExec_t exec = nullptr;
-  le_status st = capture(s, (int)nsteps, &ev, &exec);
-  if (st == LE_OK) {
+  le_status st = LE_OK;
+  if (s->eager) {
     CK(cudaEventRecord(t0, s->stream));
-    CK(cudaGraphLaunch(exec, s->stream));
+    for (int64_t k = 0; k < nsteps && st == LE_OK; ++k) st = eager_step(s, &ev[4 * k]);
     CK(cudaEventRecord(t1, s->stream));
     launch_fold(s->s, s->stream);
-    st = read_dyn(s);
+    if (st == LE_OK) st = read_dyn(s);
+  } else {
+    st = capture(s, (int)nsteps, &ev, &exec);
+    if (st == LE_OK) {
+      CK(cudaEventRecord(t0, s->stream));
+      CK(cudaGraphLaunch(exec, s->stream));
+      CK(cudaEventRecord(t1, s->stream));
+      launch_fold(s->s, s->stream);
+      st = read_dyn(s);
+    }
   }
   if (st == LE_OK) {
     double fsum = 0, isum = 0;

@@ -15,14 +15,16 @@
 //   the same unwrapped coordinate, which is the wrapped peculiar velocity
 //   exactly (both v and v_s shift by shear_rate*Lz across the face).
 //
-//   A neighbour-list entry is (j | slot << 25): slot names the image of j as
-//   seen from i's build cell: an x-cell offset k in [-2,2], y and z cell
-//   offsets in [-1,1] and whether the pair straddles the top/bottom face.  The
-//   separation is d = p_i - p_j + off[slot] with a per-step table
+//   A neighbour-list entry is (j | slot << 24): slot names the image of j as
+//   seen from i's build cell, as bit fields: an x-cell offset k in [-2,2]
+//   (3 bits), y and z cell offsets in [-1,1] (2 bits each) and whether the
+//   pair straddles the top/bottom face (1 bit).  The separation is
+//   d = p_i - p_j + off(slot) with
 //       off = (k*lx + cross*dcz*s(t), dcy*ly, dcz*lz),
 //   s(t) = f_b + (dX(t) - dX(t_b)), f_b = dX(t_b) mod lx: the image offset of
-//   Eq. 4 enters only through the table, so the pair loop has no minimum-image
-//   arithmetic and no FP64.
+//   Eq. 4 enters only through s(t), so the pair loop has no minimum-image
+//   arithmetic and no FP64; the pair kernel decodes the offset from the bit
+//   fields with a few ALU operations instead of a table lookup.
 #pragma once
 
 #include <cstdint>
@@ -30,10 +32,10 @@
 
 namespace le {
 
-constexpr int kIndexBits = 25;
+constexpr int kIndexBits = 24;
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
-constexpr int kNumSlots = 90;
-// end marker of a particle's bond entries (slot 127 is never a valid code)
+constexpr int kNumSlots = 256;   // 8-bit slot codes (90 of them are used)
+// end marker of a particle's bond entries (slot 255 is never a valid code)
 constexpr uint32_t kNoBond = 0xFFFFFFFFu;
 constexpr int kMaxBonds = 8;
 constexpr int kMaxBins = 1024;
@@ -52,20 +54,40 @@ enum ErrBits : int {
   kErrNonfinite = 2,  // a force or velocity is NaN/Inf
   kErrCapacity = 4,   // neighbour list overflow
   kErrSlot = 8,       // a bonded pair outside the 90-slot window
+  kErrTimeout = 16,   // a bounded wait on a bulk copy gave up
 };
 
 __host__ __device__ inline int slot_code(int k, int dcy, int dcz, int cross) {
-  return (k + 2) + 5 * ((dcy + 1) + 3 * ((dcz + 1) + 3 * cross));
+  return (k + 2) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7);
 }
 
 __host__ __device__ inline void slot_decode(int s, int &k, int &dcy, int &dcz, int &cross) {
-  k = s % 5 - 2;
-  s /= 5;
-  dcy = s % 3 - 1;
-  s /= 3;
-  dcz = s % 3 - 1;
-  cross = s / 3;
+  k = (s & 7) - 2;
+  dcy = ((s >> 3) & 3) - 1;
+  dcz = ((s >> 5) & 3) - 1;
+  cross = (s >> 7) & 1;
 }
+
+// Kernel constants in one precision, computed on the host so that no kernel
+// evaluates FP64 divisions or square roots per thread (FP64 runs at 1/64 of
+// the FP32 rate on this part).
+template <class R> struct KConst {
+  R half_dt_m;    // dt / (2m)
+  R dt;
+  R rc2;          // rc^2
+  R sig2;         // sigma^2
+  R eps24;        // 24 eps
+  R amp;          // sqrt(24 xi kT m / dt): random-force amplitude (Eq. 5/7 pattern)
+  R xim;          // xi m
+  R shear;        // shear rate
+  R half_Lz;
+  R Lz;
+  R shear_Lz;     // shear rate * Lz (velocity jump)
+  R R02;          // FENE R0^2
+  R fene_k;
+  R mass;
+  R bins_per_Lz;  // nbins / Lz
+};
 
 // Constant per-system parameters, passed to every kernel by value.
 struct Geom {
@@ -82,7 +104,17 @@ struct Geom {
   int thermostat, lj_shift, nbins, sample_every;
   int sort_bits;                  // bits of the largest cell index
   uint64_t seed, system;
+  float rl2_build;                // (rl (1 + 1e-5))^2: list radius with a rounding margin
+  float inv_lc[3];                // 1 / cell edge
+  float half_lc_f[3];             // half cell edge with a rounding margin (list pruning)
+  float lc_hi[3], lc_lo[3];       // cell edge as an unevaluated float sum
+  KConst<float> cf;
+  KConst<double> cd;
 };
+
+template <class R> __device__ __forceinline__ const KConst<R> &kc(const Geom &g);
+template <> __device__ __forceinline__ const KConst<float> &kc<float>(const Geom &g) { return g.cf; }
+template <> __device__ __forceinline__ const KConst<double> &kc<double>(const Geom &g) { return g.cd; }
 
 // Device-resident dynamic record of one system (one per handle).
 struct Dyn {
@@ -92,7 +124,9 @@ struct Dyn {
   double dX_build;       // dX(build_step)
   double f_build;        // dX(build_step) - m_build * lx, in [0, lx)
   double s;              // continuous cross-face shift of this step
+  float f_hi, f_lo;      // f_build as an unevaluated float sum (FP32 re-basing)
   int m_build;
+  int win_lo[2], win_hi[2];  // x-cell window of rows across the top/bottom face, [dcz=-1, dcz=+1]
   int cur;               // buffer set holding the current state
   unsigned maxdisp2;     // float bits of max |p - p_build|^2 this step
   int rebuild;           // 1 if this step rebuilt the lists
@@ -136,8 +170,9 @@ struct Work {
   uint32_t *bond_e;        // [n][maxb] bond entries of sorted slots (kNoBond: none)
   int *bond_gid;           // [n][maxb] bond partners by particle id (-1: none)
   int *rank;               // [n] sorted slot of each particle id
-  double *X;               // [3n] FP64 wrapped positions, pre-sort order
-  double *Xs;              // [3n] FP64 wrapped positions, sorted order
+  void *tmp_p;             // [n] re-based displacement (Vec<R>), pre-sort order
+  float4 *tmp_lo;          // [n] FP32 mode: its low parts
+  double *Xs;              // [3n] FP64 build positions, sorted order (bonded systems)
   uint32_t *key[2], *val[2];  // radix-sort ping-pong buffers
   uint32_t *hist;          // radix-sort digit counts
   long long *acc_prof;     // [2*nbins] per-step fixed-point vx sums and counts

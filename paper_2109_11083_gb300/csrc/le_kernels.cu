@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float disp2 = 0.f;
   if (i < g.n) {
-    const R half = R(0.5 * g.dt / g.mass);
-    const R dt = R(g.dt);
+    const R half = kc<R>(g).half_dt_m;
+    const R dt = kc<R>(g).dt;
     V4<R> v = b.v[i];
     const V4<R> f = b.ft[i];
     v.x += half * f.x;
@@ -163,12 +163,24 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
   }
 }
 
+// x-cell window of the neighbour rows across the top/bottom face for a build
+// with f_b = dX(t_b) mod lx: every cell whose image lies within rl of the
+// shifted row (3 or 4 cells; index 0 for dcz = -1, 1 for dcz = +1).
+__device__ __forceinline__ void cross_window(const Geom &g, double fb, Dyn *d) {
+  const double phi = fb / g.lc[0];
+  const double rho = g.rl / g.lc[0] * (1.0 + 1e-5) + 1e-9;
+  d->win_lo[1] = phi > 1.0 - rho ? -2 : -1;
+  d->win_hi[1] = phi < rho ? 1 : 0;
+  d->win_lo[0] = phi < rho ? -1 : 0;
+  d->win_hi[0] = phi > 1.0 - rho ? 2 : 1;
+}
+
 // ------------------------------------------------------------------ k_decide
 // One block.  Folds the previous step's fixed-point samples into the running
 // sums, advances the step, evaluates the rebuild trigger and fills the slot
 // offset table.
 __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Work w,
-                                                cudaGraphConditionalHandle h) {
+                                                cudaGraphConditionalHandle h, int use_cond) {
   __shared__ double s_sh;
   __shared__ int need_sh;
   const int t = threadIdx.x;
@@ -213,9 +225,12 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
       if (f < 0.0) { f += g.lc[0]; m -= 1; }
       d->m_build = m;
       d->f_build = f;
+      d->f_hi = (float)f;
+      d->f_lo = (float)(f - (double)d->f_hi);
       d->dX_build = dX1;
       d->build_step = n1;
       d->list_entries = 0;
+      cross_window(g, f, d);
       d->nrebuild += 1;
       if (!disp_need && !d->force_rebuild) d->nimage += 1;
       s = f;
@@ -229,7 +244,7 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
     d->force_rebuild = 0;
     s_sh = s;
     need_sh = need ? 1 : 0;
-    cudaGraphSetConditional(h, need ? 1u : 0u);
+    if (use_cond) cudaGraphSetConditional(h, need ? 1u : 0u);
   }
   __syncthreads();
   const double s = s_sh;
@@ -277,66 +292,195 @@ __global__ void k_fold(Geom g, Dyn *__restrict__ d, Work w) {
 }
 
 // ------------------------------------------------------------------ k_force
+// Bulk-copy (TMA, cp.async.bulk) helpers for streaming a warp's neighbour-list
+// rows into shared memory.  Waits are bounded: after kWaitLimit polls the
+// kernel records kErrTimeout instead of spinning on.
+constexpr int kRowsPerChunk = 16;                  // 16 rows x 128 B = 2 KB per stage
+constexpr int kForceWarps = kForceThreads / 32;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_rows(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Image offset of a slot (bit fields, see le_common.cuh) from the cell edges
+// and the cross-face shift s of this step: a handful of ALU operations.
+template <class R> struct SlotGeo {
+  R lx, ly, lz, s;
+};
+template <class R>
+__device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &ox, R &oy, R &oz) {
+  const int slot = (int)(e >> kIndexBits);
+  const int k = (slot & 7) - 2;
+  const int dcy = ((slot >> 3) & 3) - 1;
+  const int dcz = ((slot >> 5) & 3) - 1;
+  const int cz = (slot & 128) ? dcz : 0;
+  ox = R(k) * G.lx + R(cz) * G.s;
+  oy = R(dcy) * G.ly;
+  oz = R(dcz) * G.lz;
+}
+
+template <class R>
+__device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
+                                        const SlotGeo<R> &G, R rc2, R sig2, R eps24, R &fx,
+                                        R &fy, R &fz, R &vir) {
+  R ox, oy, oz;
+  slot_offset<R>(e, G, ox, oy, oz);
+  const R dx = (pi.x - pj.x) + ox;
+  const R dy = (pi.y - pj.y) + oy;
+  const R dz = (pi.z - pj.z) + oz;
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 < rc2) {
+    const R ir2 = R(1) / r2;
+    const R s2 = sig2 * ir2;
+    const R s6 = s2 * s2 * s2;
+    const R fr = eps24 * ir2 * s6 * (R(2) * s6 - R(1));
+    const R tx = fr * dx;
+    fx += tx;
+    fy += fr * dy;
+    fz += fr * dz;
+    vir += tx * dz;
+  }
+}
+
+// One thread per particle; each warp streams its 32 particles' list rows
+// (column-major: row k holds entry k of all 32 lanes, 128 B) through a
+// two-stage shared-memory ring filled by bulk copies, and gathers neighbour
+// positions four at a time.
 template <class R, bool BONDS>
 __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
-  __shared__ V4<R> s_off[kNumSlots];
-  __shared__ double s_red[2][kForceThreads / 32];
+  __shared__ double s_red[2][kForceWarps];
+  __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
+  __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
   extern __shared__ long long s_prof[];  // [2 * nbins]
-  const int t = threadIdx.x;
-  for (int e = t; e < kNumSlots; e += blockDim.x)
-    s_off[e] = make4<R>(R(d->off[e][0]), R(d->off[e][1]), R(d->off[e][2]), R(0));
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cur = d->cur;
   const long long n1 = d->step;
+  SlotGeo<R> G;
+  G.lx = R(g.lc[0]);
+  G.ly = R(g.lc[1]);
+  G.lz = R(g.lc[2]);
+  G.s = R(d->s);
   const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
     for (int b = t; b < 2 * g.nbins; b += blockDim.x) s_prof[b] = 0;
+  if (lane == 0) {
+    mbar_init(&s_bar[warp][0], 1);
+    mbar_init(&s_bar[warp][1], 1);
+  }
+  mbar_init_fence();
   __syncthreads();
 
   const Bufs<R> b = pick(cur, s0, s1);
+  const KConst<R> &K = kc<R>(g);
   const int i = blockIdx.x * blockDim.x + t;
+  const bool active = i < g.n;
+  const int cnt = active ? min(w.ncount[i], g.maxnb) : 0;
+  int kmax = cnt;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  const int nchunks = (kmax + kRowsPerChunk - 1) / kRowsPerChunk;
+  const uint32_t *wrows = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u;
+  auto issue = [&](int c) {
+    const int r0 = c * kRowsPerChunk;
+    const int rows = min(kRowsPerChunk, kmax - r0);
+    bulk_rows(&s_rows[warp][c & 1][0][0], wrows + (size_t)r0 * 32u, (uint32_t)rows * 128u,
+              &s_bar[warp][c & 1]);
+  };
+  if (lane == 0)
+    for (int c = 0; c < min(2, nchunks); ++c) issue(c);
+
+  const R rc2 = K.rc2, sig2 = K.sig2, eps24 = K.eps24;
+  R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
+  V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
+  if (active) pi = b.p[i];
+  bool ok = true;
+  int waited = 0;  // chunks whose barrier has been passed
+  for (int c = 0; c < nchunks; ++c) {
+    const int st = c & 1;
+    if (!mbar_wait(&s_bar[warp][st], (uint32_t)(c >> 1) & 1u)) {
+      ok = false;
+      break;
+    }
+    waited = c + 1;
+    const uint32_t(*rows)[32] = s_rows[warp][st];
+    const int rn = min(kRowsPerChunk, cnt - c * kRowsPerChunk);
+    int r = 0;
+    for (; r + 4 <= rn; r += 4) {
+      const uint32_t e0 = rows[r][lane], e1 = rows[r + 1][lane];
+      const uint32_t e2 = rows[r + 2][lane], e3 = rows[r + 3][lane];
+      const V4<R> q0 = load4(b.p + (e0 & kIndexMask));
+      const V4<R> q1 = load4(b.p + (e1 & kIndexMask));
+      const V4<R> q2 = load4(b.p + (e2 & kIndexMask));
+      const V4<R> q3 = load4(b.p + (e3 & kIndexMask));
+      lj_pair<R>(pi, q0, e0, G, rc2, sig2, eps24, fx, fy, fz, vir);
+      lj_pair<R>(pi, q1, e1, G, rc2, sig2, eps24, fx, fy, fz, vir);
+      lj_pair<R>(pi, q2, e2, G, rc2, sig2, eps24, fx, fy, fz, vir);
+      lj_pair<R>(pi, q3, e3, G, rc2, sig2, eps24, fx, fy, fz, vir);
+    }
+    for (; r < rn; ++r) {
+      const uint32_t e = rows[r][lane];
+      const V4<R> q = load4(b.p + (e & kIndexMask));
+      lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, fx, fy, fz, vir);
+    }
+    __syncwarp();
+    if (lane == 0 && c + 2 < nchunks) {
+      fence_async_smem();  // the rows just read are overwritten by the async proxy
+      issue(c + 2);
+    }
+  }
+  if (!ok) {
+    atomicOr(&d->err, (int)kErrTimeout);
+    // let copies still in flight land before the block's shared memory is released
+    for (int c = waited; c < min(waited + 2, nchunks); ++c)
+      mbar_wait(&s_bar[warp][c & 1], (uint32_t)(c >> 1) & 1u);
+  }
+
   R sxz = R(0), ke = R(0);
   int bin = -1;
   R vxw = R(0);
-  if (i < g.n) {
-    const V4<R> pi = b.p[i];
-    const int cnt = min(w.ncount[i], g.maxnb);
-    const uint32_t *nl = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
-    const R rc2 = R(g.rc * g.rc), sig2 = R(g.sigma * g.sigma), eps24 = R(24.0 * g.eps);
-    R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
-    for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = __ldg(nl + (size_t)k * 32u);
-      const int j = (int)(e & kIndexMask);
-      const V4<R> pj = load4(b.p + j);
-      const V4<R> o = s_off[e >> kIndexBits];
-      const R dx = (pi.x - pj.x) + o.x;
-      const R dy = (pi.y - pj.y) + o.y;
-      const R dz = (pi.z - pj.z) + o.z;
-      const R r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < rc2) {
-        const R ir2 = R(1) / r2;
-        const R s2 = sig2 * ir2;
-        const R s6 = s2 * s2 * s2;
-        const R fr = eps24 * ir2 * s6 * (R(2) * s6 - R(1));
-        const R tx = fr * dx;
-        fx += tx;
-        fy += fr * dy;
-        fz += fr * dz;
-        vir += tx * dz;
-      }
-    }
+  if (active) {
     if constexpr (BONDS) {
-      const R R02 = R(g.fene_R0 * g.fene_R0), kf = R(g.fene_k);
+      const R R02 = K.R02, kf = K.fene_k;
       for (int q = 0; q < g.maxb; ++q) {
         const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
         if (e == kNoBond) break;
         const int j = (int)(e & kIndexMask);
         const V4<R> pj = load4(b.p + j);
-        const V4<R> o = s_off[e >> kIndexBits];
-        const R dx = (pi.x - pj.x) + o.x;
-        const R dy = (pi.y - pj.y) + o.y;
-        const R dz = (pi.z - pj.z) + o.z;
+        R ox, oy, oz;
+        slot_offset<R>(e, G, ox, oy, oz);
+        const R dx = (pi.x - pj.x) + ox;
+        const R dy = (pi.y - pj.y) + oy;
+        const R dz = (pi.z - pj.z) + oz;
         const R x = R(1) - (dx * dx + dy * dy + dz * dz) / R02;
         if (!(x > R(0))) {
           atomicOr(&d->err, (int)kErrBond);
@@ -353,20 +497,20 @@ __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict
     // Eq. 5: friction on the peculiar velocity plus the random force
     const V4<R> v = b.v[i];
     const R zu = pi.z + pi.w;  // unwrapped z (reference + displacement)
-    const R vs = R(g.shear_rate) * (zu - R(0.5 * g.L[2]));
+    const R vs = K.shear * (zu - K.half_Lz);
     R ftx = fx, fty = fy, ftz = fz;
     if (g.thermostat == 1) {
       R u[3];
       uniform3<R>(g, n1, b.gid[i], u);
-      const R amp = R(sqrt(24.0 * g.xi * g.kT * g.mass / g.dt));
-      const R xm = R(g.xi * g.mass);
+      const R amp = K.amp;
+      const R xm = K.xim;
       ftx += -xm * (v.x - vs) + amp * u[0];
       fty += -xm * v.y + amp * u[1];
       ftz += -xm * v.z + amp * u[2];
     }
     V4<R> nv = v;
     if (mode == 0) {
-      const R half = R(0.5 * g.dt / g.mass);
+      const R half = K.half_dt_m;
       nv.x = v.x + half * ftx;
       nv.y = v.y + half * fty;
       nv.z = v.z + half * ftz;
@@ -377,20 +521,21 @@ __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict
     if (!isfinite(ftx + fty + ftz) || !isfinite(nv.x + nv.y + nv.z))
       atomicOr(&d->err, (int)kErrNonfinite);
     if (sample) {
-      const R m = R(g.mass);
+      const R m = K.mass;
       const R vpx = nv.x - vs;
       sxz = m * vpx * nv.z + R(0.5) * vir;
       ke = m * (vpx * vpx + nv.y * nv.y + nv.z * nv.z);
       R zw = zu, vw = nv.x;
-      const R Lz = R(g.L[2]);
+      const R Lz = K.Lz;
       if (zw >= Lz) {
         zw -= Lz;
-        vw -= R(g.shear_rate * g.L[2]);
+        vw -= K.shear_Lz;
       } else if (zw < R(0)) {
         zw += Lz;
-        vw += R(g.shear_rate * g.L[2]);
+        vw += K.shear_Lz;
       }
-      int bb = (int)floor((double)zw * (double)g.nbins / g.L[2]);
+      // same operation order as the bins of the oracle: z / Lz * nbins
+      int bb = (int)floor(zw / Lz * R(g.nbins));
       bin = bb < 0 ? 0 : (bb >= g.nbins ? g.nbins - 1 : bb);
       vxw = vw;
     }
@@ -399,18 +544,35 @@ __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict
   // deterministic block sums -> fixed-point integer atomics
   double a = (double)warp_sum(sxz);
   double c = (double)warp_sum(ke);
-  if ((t & 31) == 0) {
-    s_red[0][t >> 5] = a;
-    s_red[1][t >> 5] = c;
+  if (lane == 0) {
+    s_red[0][warp] = a;
+    s_red[1][warp] = c;
   }
-  if (bin >= 0) {
-    atomicAdd((unsigned long long *)&s_prof[bin], (unsigned long long)(long long)__float2int_rn((float)vxw * (float)kFixP));
-    atomicAdd((unsigned long long *)&s_prof[g.nbins + bin], 1ull);
+  {
+    // lanes of a warp mostly share a z bin: one shared atomic per distinct
+    // bin and warp (integer sums, so the order of addition does not matter)
+    const float vc = fminf(fmaxf((float)vxw, -1000.f), 1000.f);
+    const int q = bin >= 0 ? __float2int_rn(vc * (float)kFixP) : 0;
+    unsigned todo = __ballot_sync(0xffffffffu, bin >= 0);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int b0 = __shfl_sync(0xffffffffu, bin, leader);
+      const unsigned grp = __ballot_sync(0xffffffffu, bin == b0);
+      // split the 2^20 fixed-point values so 32 of them cannot overflow int32
+      const int hi = __reduce_add_sync(0xffffffffu, bin == b0 ? (q >> 10) : 0);
+      const int lo = __reduce_add_sync(0xffffffffu, bin == b0 ? (q & 1023) : 0);
+      if (lane == leader) {
+        atomicAdd((unsigned long long *)&s_prof[b0],
+                  (unsigned long long)((long long)hi * 1024 + (long long)lo));
+        atomicAdd((unsigned long long *)&s_prof[g.nbins + b0], (unsigned long long)__popc(grp));
+      }
+      todo &= ~grp;
+    }
   }
   __syncthreads();
   if (t == 0) {
     double A = 0.0, B = 0.0;
-    for (int k = 0; k < kForceThreads / 32; ++k) {
+    for (int k = 0; k < kForceWarps; ++k) {
       A += s_red[0][k];
       B += s_red[1][k];
     }
@@ -419,41 +581,112 @@ __global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict
     if (blockIdx.x == 0) d->pending = 1;
   }
   for (int q = t; q < g.nbins; q += blockDim.x) {
-    const long long cnt = s_prof[g.nbins + q];
-    if (cnt) {
+    const long long cn = s_prof[g.nbins + q];
+    if (cn) {
       atomicAdd((unsigned long long *)&w.acc_prof[q], (unsigned long long)s_prof[q]);
-      atomicAdd((unsigned long long *)&w.acc_prof[g.nbins + q], (unsigned long long)cnt);
+      atomicAdd((unsigned long long *)&w.acc_prof[g.nbins + q], (unsigned long long)cn);
     }
   }
 }
 
 // --------------------------------------------------------------- rebuild: bin
-// Re-bases the current state: FP64 absolute position, LE wrap with the
-// velocity jump at the current offset, new cell.  Writes X (pre-sort order)
-// and the sort keys/values.
+// Re-basing without FP64 (FP32 mode): a displacement is the unevaluated sum
+// hi + lo of two floats; moving it to another cell subtracts an integer
+// number of cell edges, each edge itself split into hi + lo.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl) {
+  const float s = __fadd_rn(hi, bh);
+  const float bb = __fsub_rn(s, hi);
+  float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// (hi, lo) -= k * (eh + el) for a small integer k (the product is split exactly)
+__device__ __forceinline__ void df_sub_edges(float &hi, float &lo, int k, float eh, float el) {
+  if (k == 0) return;
+  const float fk = (float)(-k);
+  const float t = __fmul_rn(fk, eh);
+  const float te = __fmaf_rn(fk, eh, -t);
+  df_add(hi, lo, t, __fmaf_rn(fk, el, te));
+}
+
+template <class R> struct Disp;   // a displacement being re-based
+template <> struct Disp<float> {
+  float h[3], l[3];
+  __device__ void sub_edges(const Geom &g, int a, int k) { df_sub_edges(h[a], l[a], k, g.lc_hi[a], g.lc_lo[a]); }
+  __device__ void sub_x(float fh, float fl) { df_add(h[0], l[0], -fh, -fl); }
+  __device__ float approx(int a) const { return h[a]; }
+};
+template <> struct Disp<double> {
+  double h[3];
+  __device__ void sub_edges(const Geom &g, int a, int k) { h[a] -= (double)k * g.lc[a]; }
+  __device__ float approx(int a) const { return (float)h[a]; }
+};
+
+__device__ __forceinline__ int wrap_index(int c, int n) {
+  c %= n;
+  return c < 0 ? c + n : c;
+}
+
+// Re-bases the current state on the cells the particles occupy now: the
+// unwrapped cell index, the LE wrap through the top/bottom face (z image
+// removed, x -= dX as m_b cells + f_b, vx -= shear_rate*Lz), periodic x/y.
+// Writes the new displacement (pre-sort order) and the sort keys/values.
 template <class R>
 __global__ void __launch_bounds__(256) k_rb_bin(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                 Bufs<R> s1, Work w) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  double x[3];
-  absolute_position<R>(g, b, i, x);
-  V4<R> v = b.v[i];
-  double vx = (double)v.x;
-  if (le_wrap(g, d->dX, x, vx) != 0) {
-    v.x = R(vx);
+  const float4 q = b.pb[i];
+  int c0, c1, c2;
+  cell_coords(g, __float_as_int(q.w), c0, c1, c2);
+  const V4<R> p = b.p[i];
+  Disp<R> u;
+  u.h[0] = p.x;
+  u.h[1] = p.y;
+  u.h[2] = p.z;
+  if constexpr (sizeof(R) == 4) {
+    const float4 lo = b.plo[i];
+    u.l[0] = lo.x;
+    u.l[1] = lo.y;
+    u.l[2] = lo.z;
+  }
+  const int dz = (int)floorf(0.5f + u.approx(2) * g.inv_lc[2]);
+  u.sub_edges(g, 2, dz);
+  int cz = c2 + dz, wz = 0;
+  if (cz >= g.nc[2]) { cz -= g.nc[2]; wz = 1; }
+  else if (cz < 0) { cz += g.nc[2]; wz = -1; }
+  cz = min(max(cz, 0), g.nc[2] - 1);
+  int cx = c0;
+  if (wz != 0) {
+    // x -= wz * dX with dX = m_b lx + f_b
+    if constexpr (sizeof(R) == 4) {
+      if (wz > 0) u.sub_x(d->f_hi, d->f_lo);
+      else u.sub_x(-d->f_hi, -d->f_lo);
+    } else {
+      u.h[0] -= (double)wz * d->f_build;
+    }
+    cx -= wz * d->m_build;
+    V4<R> v = b.v[i];
+    v.x -= R(wz) * kc<R>(g).shear_Lz;
     b.v[i] = v;
   }
-  w.X[3 * (size_t)i + 0] = x[0];
-  w.X[3 * (size_t)i + 1] = x[1];
-  w.X[3 * (size_t)i + 2] = x[2];
-  w.key[0][i] = (uint32_t)cell_of(g, x);
+  const int dx = (int)floorf(0.5f + u.approx(0) * g.inv_lc[0]);
+  u.sub_edges(g, 0, dx);
+  cx = wrap_index(cx + dx, g.nc[0]);
+  const int dy = (int)floorf(0.5f + u.approx(1) * g.inv_lc[1]);
+  u.sub_edges(g, 1, dy);
+  const int cy = wrap_index(c1 + dy, g.nc[1]);
+  w.key[0][i] = (uint32_t)(cx + g.nc[0] * (cy + g.nc[1] * cz));
   w.val[0][i] = (uint32_t)i;
+  V4<R> *tp = reinterpret_cast<V4<R> *>(w.tmp_p);
+  tp[i] = make4<R>(u.h[0], u.h[1], u.h[2], R(0));
+  if constexpr (sizeof(R) == 4) w.tmp_lo[i] = make_float4(u.l[0], u.l[1], u.l[2], 0.f);
 }
 
 // Initial load: caller-order FP64 positions/velocities (staging) wrapped as
-// images at the current offset, into the current buffer set at row i.
+// images at the current offset, binned, displacement from the cell reference.
 template <class R>
 __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                 Bufs<R> s1, Work w, const double *__restrict__ stage) {
@@ -472,10 +705,25 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
     vx -= nzf * g.shear_rate * g.L[2];
   }
   le_wrap(g, d->dX, x, vx);
-  w.X[3 * (size_t)i + 0] = x[0];
-  w.X[3 * (size_t)i + 1] = x[1];
-  w.X[3 * (size_t)i + 2] = x[2];
-  w.key[0][i] = (uint32_t)cell_of(g, x);
+  const int c = cell_of(g, x);
+  int cx, cy, cz;
+  cell_coords(g, c, cx, cy, cz);
+  const double r[3] = {((double)cx + 0.5) * g.lc[0], ((double)cy + 0.5) * g.lc[1],
+                       ((double)cz + 0.5) * g.lc[2]};
+  V4<R> *tp = reinterpret_cast<V4<R> *>(w.tmp_p);
+  if constexpr (sizeof(R) == 4) {
+    float h[3], l[3];
+    for (int a = 0; a < 3; ++a) {
+      const double dd = x[a] - r[a];
+      h[a] = (float)dd;
+      l[a] = (float)(dd - (double)h[a]);
+    }
+    tp[i] = make_float4(h[0], h[1], h[2], 0.f);
+    w.tmp_lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+  } else {
+    tp[i] = make4<double>(x[0] - r[0], x[1] - r[1], x[2] - r[2], 0.0);
+  }
+  w.key[0][i] = (uint32_t)c;
   w.val[0][i] = (uint32_t)i;
   b.v[i] = make4<R>(R(vx), R(vy), R(vz), R(0));
   b.ft[i] = make4<R>(R(0), R(0), R(0), R(0));
@@ -484,6 +732,8 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
 }
 
 // ---------------------------------------------------------- rebuild: permute
+// Gathers the re-based state into cell order.  Forces are not moved: the
+// pair kernel of the same step overwrites them before anything reads them.
 template <class R>
 __global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                     Bufs<R> s1, Work w,
@@ -496,32 +746,32 @@ __global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d,
   if (k >= g.n) return;
   const int o = min((int)sval[k], g.n - 1);
   const int c = min((int)skey[k], g.ncell - 1);
-  int cx, cy, cz;
-  cell_coords(g, c, cx, cy, cz);
-  const double X0 = w.X[3 * (size_t)o], X1 = w.X[3 * (size_t)o + 1], X2 = w.X[3 * (size_t)o + 2];
-  const double r0 = ((double)cx + 0.5) * g.lc[0];
-  const double r1 = ((double)cy + 0.5) * g.lc[1];
-  const double r2 = ((double)cz + 0.5) * g.lc[2];
-  const double p0 = X0 - r0, p1 = X1 - r1, p2 = X2 - r2;
-  if constexpr (sizeof(R) == 4) {
-    const float h0 = (float)p0, h1 = (float)p1, h2 = (float)p2;
-    dst.p[k] = make_float4(h0, h1, h2, (float)r2);
-    dst.plo[k] = make_float4((float)(p0 - (double)h0), (float)(p1 - (double)h1),
-                             (float)(p2 - (double)h2), 0.f);
-    dst.pb[k] = make_float4(h0, h1, h2, __int_as_float(c));
-  } else {
-    dst.p[k] = make4<double>(p0, p1, p2, r2);
-    dst.pb[k] = make_float4((float)p0, (float)p1, (float)p2, __int_as_float(c));
-  }
+  const int cz = c / (g.nc[0] * g.nc[1]);
+  const V4<R> h = reinterpret_cast<const V4<R> *>(w.tmp_p)[o];
+  const R zref = (R(cz) + R(0.5)) * R(g.lc[2]);
+  dst.p[k] = make4<R>(h.x, h.y, h.z, zref);
+  if constexpr (sizeof(R) == 4) dst.plo[k] = w.tmp_lo[o];
+  dst.pb[k] = make_float4((float)h.x, (float)h.y, (float)h.z, __int_as_float(c));
   dst.v[k] = src.v[o];
-  dst.ft[k] = src.ft[o];
-  dst.fc[k] = src.fc[o];
   const int gid = src.gid[o];
   dst.gid[k] = gid;
-  w.rank[gid] = k;
-  w.Xs[3 * (size_t)k] = X0;
-  w.Xs[3 * (size_t)k + 1] = X1;
-  w.Xs[3 * (size_t)k + 2] = X2;
+  if (g.maxb > 0) {
+    w.rank[gid] = k;
+    int cx, cy, czz;
+    cell_coords(g, c, cx, cy, czz);
+    double x0 = ((double)cx + 0.5) * g.lc[0] + (double)h.x;
+    double x1 = ((double)cy + 0.5) * g.lc[1] + (double)h.y;
+    double x2 = ((double)czz + 0.5) * g.lc[2] + (double)h.z;
+    if constexpr (sizeof(R) == 4) {
+      const float4 lo = w.tmp_lo[o];
+      x0 += (double)lo.x;
+      x1 += (double)lo.y;
+      x2 += (double)lo.z;
+    }
+    w.Xs[3 * (size_t)k] = x0;
+    w.Xs[3 * (size_t)k + 1] = x1;
+    w.Xs[3 * (size_t)k + 2] = x2;
+  }
 }
 
 // ----------------------------------------------------------- rebuild: ranges
@@ -558,7 +808,12 @@ __global__ void k_relist_prep(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s
 // Slot-offset tables from d->s (this step) and d->f_build (last build).
 __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
   const double s = d->s, fb = d->f_build;
-  if (threadIdx.x == 0) d->list_entries = 0;
+  if (threadIdx.x == 0) {
+    d->list_entries = 0;
+    cross_window(g, fb, d);
+    d->f_hi = (float)fb;
+    d->f_lo = (float)(fb - (double)d->f_hi);
+  }
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) {
     int k, dcy, dcz, cross;
     slot_decode(e, k, dcy, dcz, cross);
@@ -575,74 +830,86 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // (cx,cy,cz): for a y/z neighbour row inside the box, the x cells cx-1..cx+1;
 // for a row across the top/bottom face, the x window shifted by the image
 // offset: 3 or 4 cells covering every cell within rl of the shifted row
-// (f_build/lx decides whether the window reaches a 4th cell).
+// (f_build/lx decides whether the window reaches a 4th cell).  Rows and
+// cells whose box lies farther than rl from the particle are skipped.
 template <class R>
 __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                          Bufs<R> s1, Work w, int target_cur) {
-  __shared__ float4 s_off[kNumSlots];
-  for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x)
-    s_off[e] = make_float4((float)d->off_build[e][0], (float)d->off_build[e][1],
-                           (float)d->off_build[e][2], 0.f);
+  __shared__ float s_offx[kNumSlots];
+  for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
   __syncthreads();
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < g.n) {
-  const float4 qi = b.pb[i];
-  int cx, cy, cz;
-  cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
-  const float rl = (float)(g.rl * (1.0 + 1e-5));
-  const float rl2 = rl * rl;
-  const double phi = d->f_build / g.lc[0];
-  const double rho = g.rl / g.lc[0] * (1.0 + 1e-5) + 1e-9;
-  const int mb = d->m_build;
-  uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
-  for (int dcz = -1; dcz <= 1; ++dcz) {
-    int czj = cz - dcz, cross = 0;
-    if (czj < 0) { czj += g.nc[2]; cross = 1; }
-    else if (czj >= g.nc[2]) { czj -= g.nc[2]; cross = 1; }
-    int kmin = -1, kmax = 1;
-    if (cross) {
-      if (dcz > 0) {
-        kmin = phi > 1.0 - rho ? -2 : -1;
-        kmax = phi < rho ? 1 : 0;
-      } else {
-        kmin = phi < rho ? -1 : 0;
-        kmax = phi > 1.0 - rho ? 2 : 1;
+    const float4 qi = b.pb[i];
+    int cx, cy, cz;
+    cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
+    const float rl2 = g.rl2_build;
+    const float hx = g.half_lc_f[0], hy = g.half_lc_f[1], hz = g.half_lc_f[2];
+    const float ly = (float)g.lc[1], lz = (float)g.lc[2];
+    const int mb = d->m_build;
+    uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
+    for (int dcz = -1; dcz <= 1; ++dcz) {
+      const float az = qi.z + (float)dcz * lz;
+      const float gz = fmaxf(fabsf(az) - hz, 0.f);
+      if (gz * gz >= rl2) continue;
+      int czj = cz - dcz, cross = 0;
+      if (czj < 0) { czj += g.nc[2]; cross = 1; }
+      else if (czj >= g.nc[2]) { czj -= g.nc[2]; cross = 1; }
+      int kmin = -1, kmax = 1;
+      if (cross) {
+        kmin = d->win_lo[dcz > 0 ? 1 : 0];
+        kmax = d->win_hi[dcz > 0 ? 1 : 0];
       }
-    }
-    for (int dcy = -1; dcy <= 1; ++dcy) {
-      int cyj = cy - dcy;
-      cyj = ((cyj % g.nc[1]) + g.nc[1]) % g.nc[1];
-      const int rowbase = g.nc[0] * (cyj + g.nc[1] * czj);
-      for (int k = kmin; k <= kmax; ++k) {
-        int cxj = cx - k + (cross ? dcz * mb : 0);
-        cxj = ((cxj % g.nc[0]) + g.nc[0]) % g.nc[0];
-        const int slot = slot_code(k, dcy, dcz, cross);
-        const float4 o = s_off[slot];
-        const int cj = rowbase + cxj;
-        // clamped so that a corrupt range can never leave the particle arrays
-        const int j0 = min(max(w.cell_start[cj], 0), g.n);
-        const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
-        const bool self_slot = (slot == slot_code(0, 0, 0, 0));
-        for (int j = j0; j < j1; ++j) {
-          if (self_slot && j == i) continue;
-          const float4 qj = b.pb[j];
-          const float dx = (qi.x - qj.x) + o.x;
-          const float dy = (qi.y - qj.y) + o.y;
-          const float dz = (qi.z - qj.z) + o.z;
-          if (dx * dx + dy * dy + dz * dz < rl2) {
-            if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)j | ((uint32_t)slot << kIndexBits);
-            ++cnt;
+      for (int dcy = -1; dcy <= 1; ++dcy) {
+        const float ay = qi.y + (float)dcy * ly;
+        const float gy = fmaxf(fabsf(ay) - hy, 0.f);
+        const float gyz = gy * gy + gz * gz;
+        if (gyz >= rl2) continue;
+        const int cyj = wrap_index(cy - dcy, g.nc[1]);
+        const int rowbase = g.nc[0] * (cyj + g.nc[1] * czj);
+        for (int k = kmin; k <= kmax; ++k) {
+          const int slot = slot_code(k, dcy, dcz, cross);
+          const float ax = qi.x + s_offx[slot];
+          const float gx = fmaxf(fabsf(ax) - hx, 0.f);
+          if (gx * gx + gyz >= rl2) continue;
+          const int cxj = wrap_index(cx - k + (cross ? dcz * mb : 0), g.nc[0]);
+          const int cj = rowbase + cxj;
+          // clamped so that a corrupt range can never leave the particle arrays
+          const int j0 = min(max(w.cell_start[cj], 0), g.n);
+          const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
+          const bool self_slot = (slot == slot_code(0, 0, 0, 0));
+          const uint32_t tag = (uint32_t)slot << kIndexBits;
+          int j = j0;
+          for (; j + 1 < j1; j += 2) {
+            const float4 qa = __ldg(b.pb + j), qb = __ldg(b.pb + j + 1);
+            const float dxa = ax - qa.x, dya = ay - qa.y, dza = az - qa.z;
+            const float dxb = ax - qb.x, dyb = ay - qb.y, dzb = az - qb.z;
+            if (dxa * dxa + dya * dya + dza * dza < rl2 && !(self_slot && j == i)) {
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)j | tag;
+              ++cnt;
+            }
+            if (dxb * dxb + dyb * dyb + dzb * dzb < rl2 && !(self_slot && j + 1 == i)) {
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)(j + 1) | tag;
+              ++cnt;
+            }
+          }
+          if (j < j1) {
+            const float4 qa = __ldg(b.pb + j);
+            const float dxa = ax - qa.x, dya = ay - qa.y, dza = az - qa.z;
+            if (dxa * dxa + dya * dya + dza * dza < rl2 && !(self_slot && j == i)) {
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)j | tag;
+              ++cnt;
+            }
           }
         }
       }
     }
-  }
-  w.ncount[i] = cnt;
-  atomicMax(&d->list_max, cnt);
-  if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
+    w.ncount[i] = cnt;
+    atomicMax(&d->list_max, cnt);
+    if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
   }
   // total list entries (for the mean list length), one atomic per block
   __shared__ unsigned long long s_tot[kListThreads / 32];
@@ -849,8 +1116,8 @@ void launch_drift(const SysDev &s, cudaStream_t st) {
 #undef FN
 }
 
-void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, cudaStream_t st) {
-  k_decide<<<1, 128, 0, st>>>(s.g, s.dyn, s.w, h);
+void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+  k_decide<<<1, 128, 0, st>>>(s.g, s.dyn, s.w, h, use_cond);
 }
 
 void launch_fold(const SysDev &s, cudaStream_t st) { k_fold<<<1, 256, 0, st>>>(s.g, s.dyn, s.w); }
@@ -872,8 +1139,8 @@ void launch_force(const SysDev &s, int mode, cudaStream_t st) {
 
 static void rebuild_tail(const SysDev &s, cudaStream_t st) {
   const int n = s.g.n;
-  radix_sort_pairs(const_cast<uint32_t **>(s.w.key), const_cast<uint32_t **>(s.w.val), s.w.hist, n,
-                   s.sort_passes, s.sort_blocks, st);
+  radix_sort_pairs(const_cast<uint32_t **>(s.w.key), const_cast<uint32_t **>(s.w.val), s.w.hist,
+                   s.sort_part, n, s.g.sort_bits, s.sort_blocks, st);
   const uint32_t *skey = s.w.key[s.sort_passes & 1];
   const uint32_t *sval = s.w.val[s.sort_passes & 1];
   const int nb = blocks_for(n, 256);

@@ -12,8 +12,8 @@ constexpr int kListThreads = 128;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;   // keys per thread and sort tile
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kSortRadixBits = 8;
-constexpr int kSortBuckets = 1 << kSortRadixBits;
+constexpr int kSortMaxDigitBits = 9;
+constexpr int kSortBuckets = 1 << kSortMaxDigitBits;
 
 struct SysDev {
   Geom g;
@@ -24,6 +24,7 @@ struct SysDev {
   int prec = 0;         // 0: FP64, 1: FP32
   int sort_passes = 1;  // radix passes; the sorted keys end in buffer (sort_passes & 1)
   int sort_blocks = 1;
+  uint32_t *sort_part = nullptr;  // chunk sums of the count-table scan
   double *stage = nullptr;   // [6n] host<->device staging (caller order)
   double *partials = nullptr;// [observe blocks][16]
 };
@@ -31,7 +32,8 @@ struct SysDev {
 inline int blocks_for(int n, int threads) { return (n + threads - 1) / threads; }
 
 void launch_drift(const SysDev &s, cudaStream_t st);
-void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, cudaStream_t st);
+// use_cond: set the graph's conditional handle h (0 when launched outside a graph)
+void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st);
 // Rebuild pipeline.  from_import: positions come from the import staging
 // (launch_import already binned them); otherwise the current state is re-based.
 void launch_rebuild(const SysDev &s, bool from_import, cudaStream_t st);
@@ -49,7 +51,9 @@ int observe_blocks(const SysDev &s);
 void launch_observe(const SysDev &s, cudaStream_t st);    // partials[b][0:9] stress sums, [9] epot
 void launch_tables(const SysDev &s, cudaStream_t st);  // slot tables from dyn->s and dyn->f_build
 
-void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, int n, int passes,
-                      int blocks, cudaStream_t st);
+int sort_passes_for(int bits);
+size_t sort_scan_parts(int blocks);
+void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,
+                      int bits, int blocks, cudaStream_t st);
 
 }  // namespace le

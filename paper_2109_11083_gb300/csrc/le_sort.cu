@@ -1,6 +1,7 @@
 // Stable LSD radix sort of (cell key, slot) pairs: the "resort" step that
-// re-bins particles into cells at every list build.  8-bit digits, three
-// kernels per pass: per-tile digit counts, one exclusive scan over the
+// re-bins particles into cells at every list build.  Digits of up to 9 bits
+// (two passes for the 18-bit cell index of a 60^3 grid), three kernels per
+// pass: per-tile digit counts, a multi-block exclusive scan over the
 // digit-major count table, and a stable scatter in which each tile ranks its
 // keys chunk by chunk (warp match on the digit, then a per-digit prefix over
 // the warps of the block).  Stability keeps the previous order of particles
@@ -15,57 +16,112 @@ namespace le {
 namespace {
 
 constexpr int kWarps = kSortThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__restrict__ key, int n,
-                                                          int shift, int nblocks,
+                                                          int shift, int bits, int nblocks,
                                                           uint32_t *__restrict__ hist) {
   __shared__ uint32_t cnt[kSortBuckets];
-  for (int b = threadIdx.x; b < kSortBuckets; b += blockDim.x) cnt[b] = 0;
+  const int nb = 1 << bits;
+  const uint32_t mask = (uint32_t)nb - 1u;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
   const int base = blockIdx.x * kSortTile;
 #pragma unroll 4
   for (int k = 0; k < kSortItems; ++k) {
     const int i = base + k * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & (kSortBuckets - 1)], 1u);
+    if (i < n) atomicAdd(&cnt[(key[i] >> shift) & mask], 1u);
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < kSortBuckets; b += blockDim.x)
-    hist[(size_t)b * nblocks + blockIdx.x] = cnt[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(size_t)b * nblocks + blockIdx.x] = cnt[b];
 }
 
-// Exclusive scan of m counts by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ hist, int m) {
-  __shared__ uint32_t part[1024];
-  const int t = threadIdx.x;
-  const int per = (m + 1023) / 1024;
-  const int lo = t * per;
-  const int hi = min(lo + per, m);
-  uint32_t s = 0;
-  for (int i = lo; i < hi; ++i) s += hist[i];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    uint32_t v = t >= o ? part[t - o] : 0u;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+// Block-wide inclusive scan of one value per thread (1024 threads).
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
   }
-  uint32_t run = part[t] - s;
-  for (int i = lo; i < hi; ++i) {
-    const uint32_t c = hist[i];
-    hist[i] = run;
-    run += c;
+  if (lane == 31) warp_tot[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  return v + (warp > 0 ? warp_tot[warp - 1] : 0u);
+}
+
+// Pass 1 of the scan: the sum of each chunk of kScanChunk counts.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t *__restrict__ a, int m,
+                                                            uint32_t *__restrict__ part) {
+  __shared__ uint32_t wt[32];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < m) s += a[base + k];
+  const uint32_t incl = block_incl_scan(s, wt);
+  if (threadIdx.x == kScanThreads - 1) part[blockIdx.x] = incl;
+}
+
+// Pass 2: exclusive scan of the chunk sums (one block, up to 4 per thread).
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict__ part, int np) {
+  __shared__ uint32_t wt[32];
+  const int base = threadIdx.x * 4;
+  uint32_t v[4], s = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = base + k < np ? part[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t run = block_incl_scan(s, wt) - s;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < np) part[base + k] = run;
+    run += v[k];
+  }
+}
+
+// Pass 3: exclusive scan inside each chunk, offset by the chunk's start.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t *__restrict__ a, int m,
+                                                             const uint32_t *__restrict__ part) {
+  __shared__ uint32_t wt[32];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < m ? a[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t run = block_incl_scan(s, wt) - s + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < m) a[base + k] = run;
+    run += v[k];
   }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int n, int shift, int nblocks, const uint32_t *__restrict__ hist) {
+    uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks,
+    const uint32_t *__restrict__ hist) {
   __shared__ uint32_t base[kSortBuckets];          // global start of each digit for this tile
   __shared__ uint32_t wcnt[kWarps][kSortBuckets];  // per-warp counts -> per-warp offsets
   __shared__ uint32_t total[kSortBuckets];
+  const int nb = 1 << bits;
+  const uint32_t mask = (uint32_t)nb - 1u;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int b = t; b < kSortBuckets; b += blockDim.x) {
+  for (int b = t; b < nb; b += blockDim.x) {
     base[b] = hist[(size_t)b * nblocks + blockIdx.x];
     for (int w = 0; w < kWarps; ++w) wcnt[w][b] = 0;
   }
@@ -77,13 +133,13 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
     const uint32_t k = valid ? kin[i] : 0u;
     const uint32_t v = valid ? vin[i] : 0u;
     // invalid lanes get a digit outside the bucket range so they never match
-    const uint32_t dig = valid ? ((k >> shift) & (kSortBuckets - 1)) : (uint32_t)kSortBuckets + lane;
+    const uint32_t dig = valid ? ((k >> shift) & mask) : (uint32_t)kSortBuckets + lane;
     const uint32_t peers = __match_any_sync(0xffffffffu, dig);
     const uint32_t before = __popc(peers & ((1u << lane) - 1u));
     const int leader = __ffs(peers) - 1;
     if (valid && lane == leader) wcnt[warp][dig] = __popc(peers);
     __syncthreads();
-    for (int b = t; b < kSortBuckets; b += blockDim.x) {
+    for (int b = t; b < nb; b += blockDim.x) {
       uint32_t run = 0;
       for (int w = 0; w < kWarps; ++w) {
         const uint32_t x = wcnt[w][b];
@@ -101,7 +157,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
       }
     }
     __syncthreads();
-    for (int b = t; b < kSortBuckets; b += blockDim.x) {
+    for (int b = t; b < nb; b += blockDim.x) {
       base[b] += total[b];
       for (int w = 0; w < kWarps; ++w) wcnt[w][b] = 0;
     }
@@ -111,15 +167,28 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
 
 }  // namespace
 
-void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, int n, int passes,
-                      int blocks, cudaStream_t st) {
+int sort_passes_for(int bits) { return (bits + kSortMaxDigitBits - 1) / kSortMaxDigitBits; }
+
+size_t sort_scan_parts(int blocks) {
+  return ((size_t)kSortBuckets * blocks + kScanChunk - 1) / kScanChunk;
+}
+
+void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,
+                      int bits, int blocks, cudaStream_t st) {
+  const int passes = sort_passes_for(bits);
+  const int width = (bits + passes - 1) / passes;
   for (int p = 0; p < passes; ++p) {
-    const int shift = p * kSortRadixBits;
+    const int shift = p * width;
+    const int w = bits - shift < width ? bits - shift : width;
     const int in = p & 1, out = in ^ 1;
-    k_rs_hist<<<blocks, kSortThreads, 0, st>>>(key[in], n, shift, blocks, hist);
-    k_rs_scan<<<1, 1024, 0, st>>>(hist, kSortBuckets * blocks);
+    const int m = (1 << w) * blocks;
+    const int np = (m + kScanChunk - 1) / kScanChunk;
+    k_rs_hist<<<blocks, kSortThreads, 0, st>>>(key[in], n, shift, w, blocks, hist);
+    k_scan_sums<<<np, kScanThreads, 0, st>>>(hist, m, part);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(part, np);
+    k_scan_apply<<<np, kScanThreads, 0, st>>>(hist, m, part);
     k_rs_scatter<<<blocks, kSortThreads, 0, st>>>(key[in], val[in], key[out], val[out], n, shift,
-                                                  blocks, hist);
+                                                  w, blocks, hist);
   }
 }
 
