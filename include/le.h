@@ -190,6 +190,29 @@ LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms,
  * inside graphs with conditional nodes need this mode; it is slower. */
 LE_API le_status le_set_eager(le_sim *s, int eager);
 
+/* Conservative LJ forces (Eq. 9/10, no bonds) on n particles at positions
+ * pos (n x 3, host, caller order; any real coordinates, taken as images at
+ * step `step`, whose image offset is dX(step) of Eq. 4) written to forces
+ * (n x 3, host), for the box, shear rate, rc, skin and parameters of
+ * le_create (precision selects FP64 or FP32 arithmetic; the thermostat,
+ * bond and sampling fields are ignored).  No handle is needed.
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot call cudaMalloc where they need forces: a loop that must not
+ * allocate device memory (or meet an out-of-memory error) once it runs, or a
+ * host program whose device memory belongs to another pool.  It allocates
+ * nothing: all of its device buffers are carved out of one static device
+ * array of 32 MiB that every device loading this library holds until exit,
+ * which bounds n to 16,384 (fewer for very dense boxes; LE_ERR_INVALID_ARG
+ * beyond).  The first call on a device looks the array's address up; make it
+ * before any stream capture.  Calls share the array, serialise on a lock and
+ * return after their device work (on cuda_stream, NULL for the default
+ * stream) has finished; work that overlapped a call on the array would race.
+ * Errors: LE_ERR_INVALID_ARG, LE_ERR_BOX_TOO_SMALL, LE_ERR_CAPACITY,
+ * LE_ERR_NONFINITE, LE_ERR_CUDA. */
+LE_API le_status le_forces_noalloc(const double box[3], double shear_rate, double rc, double skin,
+                                   const le_params *p, int64_t step, int64_t n, const double *pos,
+                                   double *forces, void *cuda_stream);
+
 LE_API le_status le_destroy(le_sim *s);
 LE_API const char *le_last_error(const le_sim *s);
 LE_API const char *le_status_string(le_status st);

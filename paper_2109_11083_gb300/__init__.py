@@ -99,6 +99,9 @@ def lib():
                 "le_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
                 "le_set_state": (C.c_int, [_P, _P, C.c_size_t]),
                 "le_set_eager": (C.c_int, [_P, C.c_int]),
+                "le_forces_noalloc": (C.c_int, [_D, C.c_double, C.c_double, C.c_double,
+                                                C.POINTER(le_params), C.c_int64, C.c_int64,
+                                                _D, _D, _P]),
                 "le_destroy": (C.c_int, [_P]),
                 "le_last_error": (C.c_char_p, [_P]),
                 "le_status_string": (C.c_char_p, [C.c_int]),
@@ -117,7 +120,7 @@ def exported_symbols() -> list[str]:
             "le_step_profiled", "le_forces", "le_positions", "le_stress",
             "le_velocity_profile", "le_temperature", "le_reset_samples", "le_get_counters",
             "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
-            "le_status_string"]
+            "le_status_string", "le_forces_noalloc"]
 
 
 def _check(h, st: int):
@@ -248,6 +251,20 @@ def le_set_state(h: int, blob: bytes) -> None:
 
 def le_set_eager(h: int, eager: bool) -> None:
     _check(h, lib().le_set_eager(h, 1 if eager else 0))
+
+
+def le_forces_noalloc(box, shear_rate: float, rc: float, skin: float, params: le_params,
+                      step: int, pos, stream=None) -> np.ndarray:
+    """Forces at `pos` (image offset of step `step`) without any device
+    allocation: for callers that must not allocate device memory."""
+    b = _f64(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    p = _f64(pos, (-1, 3))
+    out = np.empty_like(p)
+    st = lib().le_forces_noalloc(b.ctypes.data_as(_D), float(shear_rate), float(rc), float(skin),
+                                 C.byref(params), int(step), p.shape[0], p.ctypes.data_as(_D),
+                                 out.ctypes.data_as(_D), _stream_handle(stream))
+    _check(None, st)
+    return out
 
 
 def le_destroy(h: int) -> None:
