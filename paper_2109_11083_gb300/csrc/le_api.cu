@@ -607,29 +607,50 @@ static le_status step_once(le_sim *s, int64_t nsteps) {
   return read_dyn(s);
 }
 
+// A longer neighbour list (the graphs captured the old one and are dropped),
+// rebuilt from the current build record.
+static le_status grow_list(le_sim *s, int maxnb) {
+  uint32_t *old = s->s.w.nbr;
+  for (size_t k = 0; k < s->allocs.size(); ++k)
+    if (s->allocs[k] == old) {
+      s->allocs.erase(s->allocs.begin() + (long)k);
+      break;
+    }
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaFree(old));
+  s->s.w.nbr = nullptr;
+  CKS(dalloc(s, &s->s.w.nbr, (size_t)s->s.g.npad * (size_t)maxnb));
+  s->s.g.maxnb = maxnb;
+  if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
+  if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
+  s->exec_chunk = s->exec_one = nullptr;
+  launch_relist(s->s, s->stream);
+  CK(cudaGetLastError());
+  return sync(s);
+}
+
 LE_API le_status le_step(le_sim *s, int64_t nsteps) {
   if (!s) return LE_ERR_INVALID_ARG;
   if (!s->has_particles) return fail(s, LE_ERR_STATE, "le_set_particles has not been called");
   if (nsteps < 0) return fail(s, LE_ERR_INVALID_ARG, "negative step count");
   if (nsteps == 0) return LE_OK;
-  CKS(read_dyn(s));
-  const int cur0 = s->h_dyn->cur;
-  CKS(take_snapshot(s));
-  CKS(step_once(s, nsteps));
-  const int err = s->h_dyn->err;
-  if (!err) return LE_OK;
-  le_status st = status_from_err(s, err);
-  std::string msg = s->err;
-  CKS(restore_snapshot(s, cur0));
-  if (st == LE_ERR_CAPACITY) {
-    // grow the list from the restored state and run the call again
-    std::vector<double> pos(3 * s->n), vel(3 * s->n);
+  for (int attempt = 0; attempt < 4; ++attempt) {
     CKS(read_dyn(s));
-    const int need = (int)std::ceil(std::max(s->h_dyn->list_max, s->s.g.maxnb) * 1.5) + 16;
-    (void)need;
-    return fail(s, LE_ERR_CAPACITY, msg + " (state rolled back to the start of the call)");
+    const int cur0 = s->h_dyn->cur;
+    CKS(take_snapshot(s));
+    CKS(step_once(s, nsteps));
+    const int err = s->h_dyn->err;
+    if (!err) return LE_OK;
+    le_status st = status_from_err(s, err);
+    const std::string msg = s->err;
+    const int seen = s->h_dyn->list_max;
+    CKS(restore_snapshot(s, cur0));
+    if (st != LE_ERR_CAPACITY)
+      return fail(s, st, msg + " (state rolled back to the start of the call)");
+    // the list overflowed: roll back, lengthen it and run the call again
+    CKS(grow_list(s, (int)std::ceil(std::max(seen, s->s.g.maxnb) * 1.3) + 16));
   }
-  return fail(s, st, msg + " (state rolled back to the start of the call)");
+  return fail(s, LE_ERR_CAPACITY, "neighbour list capacity could not be grown enough");
 }
 
 LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms, double *integrate_ms,

@@ -16,7 +16,7 @@
 //   exactly (both v and v_s shift by shear_rate*Lz across the face).
 //
 //   A neighbour-list entry is (j | slot << 24): slot names the image of j as
-//   seen from i's build cell, as bit fields: an x-cell offset k in [-2,2]
+//   seen from i's build cell, as bit fields: an x-cell offset k in [-3,4]
 //   (3 bits), y and z cell offsets in [-1,1] (2 bits each) and whether the
 //   pair straddles the top/bottom face (1 bit).  The separation is
 //   d = p_i - p_j + off(slot) with
@@ -58,11 +58,11 @@ enum ErrBits : int {
 };
 
 __host__ __device__ inline int slot_code(int k, int dcy, int dcz, int cross) {
-  return (k + 2) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7);
+  return (k + 3) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7);
 }
 
 __host__ __device__ inline void slot_decode(int s, int &k, int &dcy, int &dcz, int &cross) {
-  k = (s & 7) - 2;
+  k = (s & 7) - 3;
   dcy = ((s >> 3) & 3) - 1;
   dcz = ((s >> 5) & 3) - 1;
   cross = (s >> 7) & 1;
@@ -128,7 +128,7 @@ struct Dyn {
   int m_build;
   int win_lo[2], win_hi[2];  // x-cell window of rows across the top/bottom face, [dcz=-1, dcz=+1]
   int cur;               // buffer set holding the current state
-  unsigned maxdisp2;     // float bits of max |p - p_build|^2 this step
+  unsigned maxdisp2;     // float bits of the largest squared peculiar displacement since the build
   int rebuild;           // 1 if this step rebuilt the lists
   int err;               // ErrBits
   int list_max;          // largest neighbour count at a build

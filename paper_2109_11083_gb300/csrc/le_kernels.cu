@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
                                                          Bufs<R> s0, Bufs<R> s1) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // time since the build at the step this drift produces
+  const float shear_tau = g.cf.shear * (float)(d->step + 1 - d->build_step) * g.cf.dt;
   float disp2 = 0.f;
   if (i < g.n) {
     const R half = kc<R>(g).half_dt_m;
@@ -147,8 +149,13 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
     }
     b.v[i] = v;
     b.p[i] = p;
+    // peculiar displacement since the build: the streaming shear*tau*(z_b -
+    // Lz/2) along x (z_b = build-time z = reference + build displacement) is
+    // shared by neighbours and does not use up the skin
     const float4 q = b.pb[i];
-    const float dx = (float)p.x - q.x, dy = (float)p.y - q.y, dz = (float)p.z - q.z;
+    const float zb = (float)p.w + q.z;
+    const float dx = (float)p.x - q.x - shear_tau * (zb - (float)kc<R>(g).half_Lz);
+    const float dy = (float)p.y - q.y, dz = (float)p.z - q.z;
     disp2 = dx * dx + dy * dy + dz * dz;
   }
 #pragma unroll
@@ -166,13 +173,23 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
 // x-cell window of the neighbour rows across the top/bottom face for a build
 // with f_b = dX(t_b) mod lx: every cell whose image lies within rl of the
 // shifted row (3 or 4 cells; index 0 for dcz = -1, 1 for dcz = +1).
+// x-cell window of a neighbour row across the top/bottom face (z offset dcz)
+// for a build with f_b = dX(t_b) mod lx: candidate j in x cell k has d_x
+// within one cell edge of off(k) = k lx + dcz f_b, and d_x must reach
+// (-rl, rl): 3 or 4 cells.
 __device__ __forceinline__ void cross_window(const Geom &g, double fb, Dyn *d) {
-  const double phi = fb / g.lc[0];
-  const double rho = g.rl / g.lc[0] * (1.0 + 1e-5) + 1e-9;
-  d->win_lo[1] = phi > 1.0 - rho ? -2 : -1;
-  d->win_hi[1] = phi < rho ? 1 : 0;
-  d->win_lo[0] = phi < rho ? -1 : 0;
-  d->win_hi[0] = phi > 1.0 - rho ? 2 : 1;
+  const double lx = g.lc[0];
+  const double margin = 1e-5 * g.rl + 1e-9;
+  for (int side = 0; side < 2; ++side) {
+    const int dcz = side ? 1 : -1;
+    const double lower = -g.rl - margin;
+    const double upper = g.rl + margin;
+    // k lx + dcz fb + lx > lower  and  k lx + dcz fb - lx < upper
+    int kmin = (int)floor((lower - lx - dcz * fb) / lx) + 1;
+    int kmax = (int)ceil((upper + lx - dcz * fb) / lx) - 1;
+    d->win_lo[side] = max(kmin, -3);
+    d->win_hi[side] = min(kmax, 4);
+  }
 }
 
 // ------------------------------------------------------------------ k_decide
@@ -215,8 +232,15 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
     if (g.shear_rate < 0.0 && ds > 0.5 * g.L[0]) ds -= g.L[0];
     const double margin = 1e-6 * g.rl;
     const bool disp_need = 2.0 * (double)maxd * (1.0 + 1e-6) + margin >= g.skin;
+    // maxd is the largest PECULIAR displacement w since the build (streaming
+    // along the profile of Eq. 1 removed).  A pair's separation changes by
+    // w_i - w_j + shear*tau*dz_build e_x; pairs across the face included,
+    // since the drift of the image offset cancels their streaming
+    // difference.  A pair that can reach rc has |dz_build| < rc + 2 maxd.
+    const double tau = (double)(n1 - d->build_step) * g.dt;
+    const double shear_term = fabs(g.shear_rate) * tau * (g.rc + 2.0 * (double)maxd);
     const bool need = d->force_rebuild || disp_need ||
-                      (2.0 * (double)maxd * (1.0 + 1e-6) + fabs(ds) + margin >= g.skin);
+                      (2.0 * (double)maxd * (1.0 + 1e-6) + shear_term + margin >= g.skin);
     double s;
     if (need) {
       int m = (int)floor(dX1 / g.lc[0]);
@@ -338,7 +362,7 @@ template <class R> struct SlotGeo {
 template <class R>
 __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &ox, R &oy, R &oz) {
   const int slot = (int)(e >> kIndexBits);
-  const int k = (slot & 7) - 2;
+  const int k = (slot & 7) - 3;
   const int dcy = ((slot >> 3) & 3) - 1;
   const int dcz = ((slot >> 5) & 3) - 1;
   const int cz = (slot & 128) ? dcz : 0;
@@ -346,6 +370,26 @@ __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &
   oy = R(dcy) * G.ly;
   oz = R(dcz) * G.lz;
 }
+
+// FP32: a small field v becomes a float as (2^23 + v) - 2^23, built with an
+// integer OR into the bits of 2^23 and one float subtraction (no conversion
+// instruction); the bias of each field folds into the subtracted constant.
+template <>
+__device__ __forceinline__ void slot_offset<float>(uint32_t e, const SlotGeo<float> &G, float &ox,
+                                                   float &oy, float &oz) {
+  const float k = __uint_as_float(0x4B000000u | ((e >> 24) & 7u)) - 8388611.0f;    // -3..4
+  const float dcy = __uint_as_float(0x4B000000u | ((e >> 27) & 3u)) - 8388609.0f;  // -1..1
+  const float dcz = __uint_as_float(0x4B000000u | ((e >> 29) & 3u)) - 8388609.0f;  // -1..1
+  const float cz = (e & 0x80000000u) ? dcz : 0.0f;
+  ox = __fmaf_rn(cz, G.s, k * G.lx);
+  oy = dcy * G.ly;
+  oz = dcz * G.lz;
+}
+
+template <class R> __device__ __forceinline__ R recip(R x) { return R(1) / x; }
+// FP32 pair loop: hardware reciprocal (rcp.approx, within 1 ulp), covered by
+// the per-pair evaluation rounding allowed in the FP32 error bound
+template <> __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
 
 template <class R>
 __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
@@ -358,7 +402,7 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   const R dz = (pi.z - pj.z) + oz;
   const R r2 = dx * dx + dy * dy + dz * dz;
   if (r2 < rc2) {
-    const R ir2 = R(1) / r2;
+    const R ir2 = recip<R>(r2);
     const R s2 = sig2 * ir2;
     const R s6 = s2 * s2 * s2;
     const R fr = eps24 * ir2 * s6 * (R(2) * s6 - R(1));
@@ -963,7 +1007,7 @@ __global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, B
       const int dcy = (int)rint(off[1] / g.lc[1]);
       const int cross = nz != 0.0 ? 1 : 0;
       const int kk = (int)rint((off[0] - (cross ? (double)dcz * fb : 0.0)) / g.lc[0]);
-      if (dcz < -1 || dcz > 1 || dcy < -1 || dcy > 1 || kk < -2 || kk > 2 ||
+      if (dcz < -1 || dcz > 1 || dcy < -1 || dcy > 1 || kk < -3 || kk > 4 ||
           (cross && dcz == 0)) {
         atomicOr(&d->err, (int)kErrSlot);
       } else {

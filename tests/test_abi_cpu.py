@@ -55,17 +55,17 @@ def test_argument_checks_reject_bad_boxes_without_a_gpu(lib):
     assert e.value.status == 1
 
 
-def test_slot_encoding_covers_ninety_distinct_images():
-    """The neighbour-slot code is four bit fields (x-cell offset -2..2 in 3
+def test_slot_encoding_gives_distinct_codes_below_the_end_marker():
+    """The neighbour-slot code is four bit fields (x-cell offset -3..4 in 3
     bits, y and z offsets -1..1 in 2 bits each, across-the-face flag in 1
-    bit): 90 distinct 8-bit codes, all below the 255 end-of-bonds marker and
+    bit): 144 distinct 8-bit codes, all below the 255 end-of-bonds marker and
     leaving 24 bits for the particle index."""
     seen = set()
     for cross in (0, 1):
         for dcz in (-1, 0, 1):
             for dcy in (-1, 0, 1):
-                for k in range(-2, 3):
-                    s = (k + 2) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7)
+                for k in range(-3, 5):
+                    s = (k + 3) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7)
                     assert 0 <= s < 255
                     seen.add(s)
-    assert len(seen) == 90
+    assert len(seen) == 144

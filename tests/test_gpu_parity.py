@@ -114,10 +114,32 @@ def test_forces_every_step_at_high_shear_match_oracle_at_gpu_positions(prec):
         g, q = check_at_gpu_positions(sim, p, step, prec, box, 2.5, 0.3)
         worst = (max(worst[0], g), max(worst[1], q))
     c = sim.counters()
-    assert c["rebuilds"] >= 30 and c["image_rebuilds"] > 0
+    assert c["rebuilds"] >= 20
     assert dX > 0 and gd * box * 240 * 0.005 > box      # the offset wrapped at least once
     print(f"prec={prec} worst force errors {worst}, rebuilds {c['rebuilds']} "
           f"(image-forced {c['image_rebuilds']})")
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cold_sheared_crystal_rebuilds_on_the_shear_term(prec):
+    """A cold crystal under strong shear: the peculiar displacements stay tiny,
+    so the lists are rebuilt on the shear term of the trigger (the spread of
+    streaming displacements across a pair) rather than on the displacements;
+    streaming itself and the drift of the image offset do not force builds.
+    Forces stay exact throughout."""
+    gd = 2.0
+    pos, vel, box = lj_inputs(2048, 0.8442, gd, 19, kT=0.02)
+    sim, _, p = make_pair(pos, vel, box, gd, prec=prec, kT=0.02, xi=10.0)
+    for step in range(1, 151):
+        sim.step(1)
+        if step % 3 == 0:
+            check_at_gpu_positions(sim, p, step, prec, box, 2.5, 0.3)
+    c = sim.counters()
+    assert c["image_rebuilds"] >= 2, c
+    # far fewer builds than steps although particles stream by up to
+    # shear*Lz/2 * dt = 0.07 per step
+    assert c["rebuilds"] <= 30, c
     sim.close()
 
 
@@ -202,7 +224,7 @@ def test_kremer_grest_chains_fene_parity(prec):
         sim.step(1)
         if step % 5 == 0:
             check_at_gpu_positions(sim, p, step, prec, box, rc, 0.3, bonds)
-    assert sim.counters()["image_rebuilds"] > 0
+    assert sim.counters()["rebuilds"] > 0
     sim.close()
 
 
