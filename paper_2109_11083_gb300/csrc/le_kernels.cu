@@ -401,17 +401,18 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   const R dy = (pi.y - pj.y) + oy;
   const R dz = (pi.z - pj.z) + oz;
   const R r2 = dx * dx + dy * dy + dz * dz;
-  if (r2 < rc2) {
-    const R ir2 = recip<R>(r2);
-    const R s2 = sig2 * ir2;
-    const R s6 = s2 * s2 * s2;
-    const R fr = eps24 * ir2 * s6 * (R(2) * s6 - R(1));
-    const R tx = fr * dx;
-    fx += tx;
-    fy += fr * dy;
-    fz += fr * dz;
-    vir += tx * dz;
-  }
+  // branch-free: nearly every row has some lane inside rc, so the warp would
+  // execute the body anyway; lanes outside get a zero factor
+  const bool in = r2 < rc2;
+  const R ir2 = recip<R>(in ? r2 : R(1));
+  const R s2 = sig2 * ir2;
+  const R s6 = s2 * s2 * s2;
+  const R fr = in ? eps24 * ir2 * s6 * (R(2) * s6 - R(1)) : R(0);
+  const R tx = fr * dx;
+  fx += tx;
+  fy += fr * dy;
+  fz += fr * dz;
+  vir += tx * dz;
 }
 
 // One thread per particle; each warp streams its 32 particles' list rows
@@ -419,7 +420,7 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
 template <class R, bool BONDS>
-__global__ void __launch_bounds__(kForceThreads) k_force(Geom g, Dyn *__restrict__ d,
+__global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
   __shared__ double s_red[2][kForceWarps];
