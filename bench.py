@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels without CUDA graphs (for profilers that cannot see "
                          "kernels inside conditional graphs)")
+    ap.add_argument("--workload", default="box", choices=["box", "batched", "served"],
+                    help="box: the 4,194,304-particle LJ box (the benchmark line); batched: "
+                         "256 uneven LJ boxes stepped alone vs in one batch; served: the "
+                         "shear-sweep request stream with continuous batching")
+    ap.add_argument("--systems", type=int, default=256, help="batched workload: box count")
     ap.add_argument("--particles", type=int, default=4194304,
                     help="box size (the default is the benchmark workload; smaller boxes "
                          "of the same density are for profiler captures)")
@@ -324,10 +329,77 @@ def run_ours(args):
     return 0
 
 
+def make_box_sim(le, spec, stream=None):
+    """One LJ box of the batched workload (fcc, MB velocities + shear profile)."""
+    pos, box = synth.lj_box(spec["n"], spec["rho"], spec["seed"])
+    vel = synth.mb_velocities(spec["n"], 1.0, spec["seed"])
+    gd = spec["shear_rate"]
+    vel[:, 0] += gd * (pos[:, 2] - 0.5 * box)
+    sim = le.Sim(box, gd, 2.5, 0.3, stream=stream, dt=0.005, xi=1.0, kT=1.0, seed=spec["seed"],
+                 system_id=spec["seed"], precision=le.LE_FP32, profile_bins=20)
+    sim.set_particles(pos, vel)
+    return sim
+
+
+def run_batched(args):
+    """Config 4: independent LJ boxes of uneven N stepped one handle at a time
+    (plain) and all together in one batch, equal accuracy checked bitwise."""
+    import torch
+    import paper_2109_11083_gb300 as le
+    specs = synth.batched_systems(count=args.systems)
+    total = sum(s["n"] for s in specs)
+    plain = [make_box_sim(le, s) for s in specs]
+    batched = [make_box_sim(le, s) for s in specs]
+    w = max(args.warmup, 3)
+    for s in plain:
+        s.step(w)
+    b = le.Batch()
+    for s in batched:
+        b.add(s)
+    b.step(w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in plain:
+        s.step(args.steps)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b.step(args.steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    equal = True
+    for k in range(0, len(specs), max(1, len(specs) // 16)):
+        rp, vp = plain[k].positions()
+        rb, vb = batched[k].positions()
+        equal = equal and bool(np.array_equal(rp, rb) and np.array_equal(vp, vb))
+    value = total * args.steps / t_batch
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": w, "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched_{len(specs)}_uneven_lj_fp32", "systems": len(specs),
+                       "total_particles": total, "n_range": [500, 32000],
+                       "density_range": [0.7, 0.9], "shear_range": [1e-3, 1.0], "rc": 2.5,
+                       "skin": 0.3, "dt": 0.005},
+            "plain": {"value": total * args.steps / t_plain, "unit": UNIT,
+                      "what": "each box stepped by its own le_step, one after another"},
+            "batched_over_plain": t_plain / t_batch,
+            "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16}}
+    print(json.dumps(line), flush=True)
+    b.close()
+    for s in plain + batched:
+        s.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        from paper_2109_11083_gb300 import serve
+        return serve.main_bench(args)
     return run_ours(args)
 
 

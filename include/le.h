@@ -190,6 +190,35 @@ LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms,
  * inside graphs with conditional nodes need this mode; it is slower. */
 LE_API le_status le_set_eager(le_sim *s, int eager);
 
+/* Device memory (bytes) a handle with these parameters and n particles
+ * (nbonds bonds) would hold after le_set_particles, including the rollback
+ * snapshot taken by le_step: for admission against a memory budget. */
+LE_API le_status le_estimate_device_bytes(const double box[3], double shear_rate, double rc,
+                                          double skin, const le_params *p, int64_t n,
+                                          int64_t nbonds, size_t *bytes);
+
+/* ---------------------------------------------------------------- batches
+ * A batch advances many independent handles (boxes of uneven size, shear
+ * rates, parameters) with ONE CUDA-graph launch per 16 steps: every member's
+ * step chain (the same kernels as le_step, including the device-decided
+ * rebuild branch) is a separate branch of the graph, so members run
+ * concurrently on the device.  Each member's trajectory is bit-identical to
+ * stepping it alone with le_step.  Members remain ordinary handles (their
+ * outputs are read with le_forces, le_stress, ...), must have particles,
+ * must not be stepped on their own while in a batch, and stay owned by the
+ * caller.  The memory budget (0: none) bounds the sum of the members'
+ * device memory; le_batch_add refuses a member beyond it with LE_ERR_OOM. */
+typedef struct le_batch le_batch;
+
+LE_API le_status le_batch_create(size_t budget_bytes, void *cuda_stream, le_batch **out);
+LE_API le_status le_batch_add(le_batch *b, le_sim *s);
+LE_API le_status le_batch_remove(le_batch *b, le_sim *s);
+/* Advances every member nsteps.  On a member's error every member is rolled
+ * back to the start of the call (list overflows are grown and retried). */
+LE_API le_status le_batch_step(le_batch *b, int64_t nsteps);
+LE_API le_status le_batch_destroy(le_batch *b);
+LE_API const char *le_batch_last_error(const le_batch *b);
+
 /* Conservative LJ forces (Eq. 9/10, no bonds) on n particles at positions
  * pos (n x 3, host, caller order; any real coordinates, taken as images at
  * step `step`, whose image offset is dX(step) of Eq. 4) written to forces

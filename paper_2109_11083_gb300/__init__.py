@@ -99,6 +99,15 @@ def lib():
                 "le_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
                 "le_set_state": (C.c_int, [_P, _P, C.c_size_t]),
                 "le_set_eager": (C.c_int, [_P, C.c_int]),
+                "le_estimate_device_bytes": (C.c_int, [_D, C.c_double, C.c_double, C.c_double,
+                                                       C.POINTER(le_params), C.c_int64,
+                                                       C.c_int64, C.POINTER(C.c_size_t)]),
+                "le_batch_create": (C.c_int, [C.c_size_t, _P, C.POINTER(_P)]),
+                "le_batch_add": (C.c_int, [_P, _P]),
+                "le_batch_remove": (C.c_int, [_P, _P]),
+                "le_batch_step": (C.c_int, [_P, C.c_int64]),
+                "le_batch_destroy": (C.c_int, [_P]),
+                "le_batch_last_error": (C.c_char_p, [_P]),
                 "le_forces_noalloc": (C.c_int, [_D, C.c_double, C.c_double, C.c_double,
                                                 C.POINTER(le_params), C.c_int64, C.c_int64,
                                                 _D, _D, _P]),
@@ -120,7 +129,9 @@ def exported_symbols() -> list[str]:
             "le_step_profiled", "le_forces", "le_positions", "le_stress",
             "le_velocity_profile", "le_temperature", "le_reset_samples", "le_get_counters",
             "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
-            "le_status_string", "le_forces_noalloc"]
+            "le_status_string", "le_forces_noalloc", "le_estimate_device_bytes",
+            "le_batch_create", "le_batch_add", "le_batch_remove", "le_batch_step",
+            "le_batch_destroy", "le_batch_last_error"]
 
 
 def _check(h, st: int):
@@ -267,6 +278,44 @@ def le_forces_noalloc(box, shear_rate: float, rc: float, skin: float, params: le
     return out
 
 
+def le_estimate_device_bytes(box, shear_rate: float, rc: float, skin: float, params: le_params,
+                             n: int, nbonds: int = 0) -> int:
+    b = _f64(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    out = C.c_size_t()
+    _check(None, lib().le_estimate_device_bytes(b.ctypes.data_as(_D), float(shear_rate), float(rc),
+                                                float(skin), C.byref(params), int(n), int(nbonds),
+                                                C.byref(out)))
+    return out.value
+
+
+def _bcheck(b, st: int):
+    if st != LE_OK:
+        msg = lib().le_batch_last_error(b).decode(errors="replace") if b else ""
+        raise LEError(st, msg)
+
+
+def le_batch_create(budget_bytes: int = 0, stream=None) -> int:
+    h = _P()
+    _bcheck(None, lib().le_batch_create(int(budget_bytes), _stream_handle(stream), C.byref(h)))
+    return h.value
+
+
+def le_batch_add(b: int, h: int) -> None:
+    _bcheck(b, lib().le_batch_add(b, h))
+
+
+def le_batch_remove(b: int, h: int) -> None:
+    _bcheck(b, lib().le_batch_remove(b, h))
+
+
+def le_batch_step(b: int, nsteps: int) -> None:
+    _bcheck(b, lib().le_batch_step(b, int(nsteps)))
+
+
+def le_batch_destroy(b: int) -> None:
+    _bcheck(None, lib().le_batch_destroy(b))
+
+
 def le_destroy(h: int) -> None:
     _check(None, lib().le_destroy(h))
 
@@ -335,6 +384,42 @@ class Sim:
         if self.h:
             le_destroy(self.h)
             self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many handles advanced together by one graph launch per 16 steps."""
+
+    def __init__(self, budget_bytes: int = 0, stream=None):
+        self.b = le_batch_create(budget_bytes, stream)
+        self.members = []
+
+    def add(self, sim: Sim):
+        le_batch_add(self.b, sim.h)
+        self.members.append(sim)
+
+    def remove(self, sim: Sim):
+        le_batch_remove(self.b, sim.h)
+        self.members.remove(sim)
+
+    def step(self, nsteps: int):
+        le_batch_step(self.b, nsteps)
+
+    def close(self):
+        if self.b:
+            le_batch_destroy(self.b)
+            self.b = 0
 
     def __enter__(self):
         return self

@@ -45,6 +45,8 @@ struct le_sim {
   Dyn *h_dyn = nullptr;              // pinned mirror of the device record
   cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
   bool eager = false;                // launch kernels directly (no graphs)
+  bool dry_run = false;              // allocate() only counts bytes
+  size_t device_bytes = 0;           // device memory of the particle buffers
   // rollback snapshot of the current buffer set and the dynamic record
   std::vector<void *> snap;
   std::string err;
@@ -75,6 +77,11 @@ le_status fail(le_sim *s, le_status st, const std::string &msg) {
 template <class T> le_status dalloc(le_sim *s, T **p, size_t count) {
   void *q = nullptr;
   size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  s->device_bytes += bytes;
+  if (s->dry_run) {  // counting only (admission by memory budget)
+    *p = nullptr;
+    return LE_OK;
+  }
   CK(cudaMalloc(&q, bytes));
   s->allocs.push_back(q);
   *p = static_cast<T *>(q);
@@ -137,6 +144,7 @@ le_status status_from_err(le_sim *s, int err) {
 // ------------------------------------------------------------- allocation
 le_status allocate(le_sim *s, int64_t n, int maxnb) {
   free_device(s);
+  s->device_bytes = 0;
   Geom &g = s->s.g;
   const int prec = s->s.prec;
   g.n = (int)n;
@@ -185,7 +193,7 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   CKS(dalloc(s, &s->s.dyn, 1));
   CKS(dalloc(s, &s->s.stage, 6 * (size_t)n));
   CKS(dalloc(s, &s->s.partials, (size_t)observe_blocks(s->s) * 16));
-  CK(cudaMallocHost(&s->h_stage, sizeof(double) * 6 * (size_t)n));
+  if (!s->dry_run) CK(cudaMallocHost(&s->h_stage, sizeof(double) * 6 * (size_t)n));
   s->n = n;
   return LE_OK;
 }
@@ -212,34 +220,99 @@ void choose_cells(le_sim *s) {
   s->s.sort_passes = sort_passes_for(bits);
 }
 
+// Per-system parameters and per-precision kernel constants.
+void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, double skin,
+               const le_params *p) {
+  const double rl = rc + skin;
+  Geom &g = s->s.g;
+  std::memset(&g, 0, sizeof g);
+  for (int a = 0; a < 3; ++a) g.L[a] = box[a];
+  g.shear_rate = shear_rate;
+  g.dt = p->dt;
+  g.mass = p->mass;
+  g.kT = p->kT;
+  g.xi = p->xi;
+  g.rc = rc;
+  g.skin = skin;
+  g.rl = rl;
+  g.eps = p->eps;
+  g.sigma = p->sigma;
+  g.fene_k = p->fene_k;
+  g.fene_R0 = p->fene_R0;
+  g.thermostat = p->thermostat;
+  g.lj_shift = p->lj_shift;
+  g.nbins = p->profile_bins;
+  g.sample_every = p->sample_every;
+  g.seed = p->seed;
+  g.system = p->system_id;
+  {
+    const double rlb = rl * (1.0 + 1e-5);
+    g.rl2_build = (float)(rlb * rlb);
+    KConst<double> &c = g.cd;
+    c.half_dt_m = 0.5 * p->dt / p->mass;
+    c.dt = p->dt;
+    c.rc2 = rc * rc;
+    c.sig2 = p->sigma * p->sigma;
+    c.eps24 = 24.0 * p->eps;
+    c.amp = std::sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
+    c.xim = p->xi * p->mass;
+    c.shear = shear_rate;
+    c.half_Lz = 0.5 * box[2];
+    c.Lz = box[2];
+    c.shear_Lz = shear_rate * box[2];
+    c.R02 = p->fene_R0 * p->fene_R0;
+    c.fene_k = p->fene_k;
+    c.mass = p->mass;
+    c.bins_per_Lz = p->profile_bins / box[2];
+    KConst<float> &f = g.cf;
+    f.half_dt_m = (float)c.half_dt_m;
+    f.dt = (float)c.dt;
+    f.rc2 = (float)c.rc2;
+    f.sig2 = (float)c.sig2;
+    f.eps24 = (float)c.eps24;
+    f.amp = (float)c.amp;
+    f.xim = (float)c.xim;
+    f.shear = (float)c.shear;
+    f.half_Lz = (float)c.half_Lz;
+    f.Lz = (float)c.Lz;
+    f.shear_Lz = (float)c.shear_Lz;
+    f.R02 = (float)c.R02;
+    f.fene_k = (float)c.fene_k;
+    f.mass = (float)c.mass;
+    f.bins_per_Lz = (float)c.bins_per_Lz;
+  }
+  s->s.prec = p->precision;
+}
+
 // ------------------------------------------------------------- graph capture
-le_status capture(le_sim *s, int steps, std::vector<cudaEvent_t> *ev, cudaGraphExec_t *out) {
-  cudaGraph_t graph = nullptr;
-  CK(cudaGraphCreate(&graph, 0));
-  std::vector<cudaGraphConditionalHandle> handles(steps);
-  for (int k = 0; k < steps; ++k) CK(cudaGraphConditionalHandleCreate(&handles[k], graph, 0, 0));
-  CK(cudaStreamBeginCaptureToGraph(s->cap_main, graph, nullptr, nullptr, 0,
-                                   cudaStreamCaptureModeThreadLocal));
+// Records `steps` steps of system s on stream st, which must already be
+// capturing into `graph`: drift, decide (sets the IF condition), IF(rebuild),
+// force.  Used for a handle's own graphs and for the branches of a batch.
+cudaError_t record_steps(le_sim *s, cudaStream_t st, cudaGraph_t graph, int steps,
+                         std::vector<cudaEvent_t> *ev) {
   cudaError_t ce = cudaSuccess;
   for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
-    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 0], s->cap_main, cudaEventRecordExternal);
-    launch_drift(s->s, s->cap_main);
-    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 1], s->cap_main, cudaEventRecordExternal);
-    launch_decide(s->s, handles[k], 1, s->cap_main);
+    cudaGraphConditionalHandle handle;
+    ce = cudaGraphConditionalHandleCreate(&handle, graph, 0, 0);
+    if (ce != cudaSuccess) break;
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 0], st, cudaEventRecordExternal);
+    launch_drift(s->s, st);
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 1], st, cudaEventRecordExternal);
+    launch_decide(s->s, handle, 1, st);
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus cs;
-    ce = cudaStreamGetCaptureInfo(s->cap_main, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    ce = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
     if (ce != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handles[k];
+    cp.conditional.handle = handle;
     cp.conditional.type = cudaGraphCondTypeIf;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
     ce = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp);
     if (ce != cudaSuccess) break;
-    ce = cudaStreamUpdateCaptureDependencies(s->cap_main, &node, nullptr, 1,
+    ce = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
                                              cudaStreamSetCaptureDependencies);
     if (ce != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
@@ -249,10 +322,19 @@ le_status capture(le_sim *s, int steps, std::vector<cudaEvent_t> *ev, cudaGraphE
     launch_rebuild(s->s, false, s->cap_side);
     ce = cudaStreamEndCapture(s->cap_side, &body);
     if (ce != cudaSuccess) break;
-    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 2], s->cap_main, cudaEventRecordExternal);
-    launch_force(s->s, 0, s->cap_main);
-    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 3], s->cap_main, cudaEventRecordExternal);
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 2], st, cudaEventRecordExternal);
+    launch_force(s->s, 0, st);
+    if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 3], st, cudaEventRecordExternal);
   }
+  return ce;
+}
+
+le_status capture(le_sim *s, int steps, std::vector<cudaEvent_t> *ev, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  CK(cudaStreamBeginCaptureToGraph(s->cap_main, graph, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = record_steps(s, s->cap_main, graph, steps, ev);
   cudaGraph_t captured = nullptr;
   cudaError_t ee = cudaStreamEndCapture(s->cap_main, &captured);
   if (ce == cudaSuccess) ce = ee;
@@ -403,63 +485,7 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
   s->rc = rc;
   s->skin = skin;
   s->prm = *p;
-  Geom &g = s->s.g;
-  std::memset(&g, 0, sizeof g);
-  for (int a = 0; a < 3; ++a) g.L[a] = box[a];
-  g.shear_rate = shear_rate;
-  g.dt = p->dt;
-  g.mass = p->mass;
-  g.kT = p->kT;
-  g.xi = p->xi;
-  g.rc = rc;
-  g.skin = skin;
-  g.rl = rl;
-  g.eps = p->eps;
-  g.sigma = p->sigma;
-  g.fene_k = p->fene_k;
-  g.fene_R0 = p->fene_R0;
-  g.thermostat = p->thermostat;
-  g.lj_shift = p->lj_shift;
-  g.nbins = p->profile_bins;
-  g.sample_every = p->sample_every;
-  g.seed = p->seed;
-  g.system = p->system_id;
-  {
-    const double rlb = rl * (1.0 + 1e-5);
-    g.rl2_build = (float)(rlb * rlb);
-    KConst<double> &c = g.cd;
-    c.half_dt_m = 0.5 * p->dt / p->mass;
-    c.dt = p->dt;
-    c.rc2 = rc * rc;
-    c.sig2 = p->sigma * p->sigma;
-    c.eps24 = 24.0 * p->eps;
-    c.amp = std::sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
-    c.xim = p->xi * p->mass;
-    c.shear = shear_rate;
-    c.half_Lz = 0.5 * box[2];
-    c.Lz = box[2];
-    c.shear_Lz = shear_rate * box[2];
-    c.R02 = p->fene_R0 * p->fene_R0;
-    c.fene_k = p->fene_k;
-    c.mass = p->mass;
-    c.bins_per_Lz = p->profile_bins / box[2];
-    KConst<float> &f = g.cf;
-    f.half_dt_m = (float)c.half_dt_m;
-    f.dt = (float)c.dt;
-    f.rc2 = (float)c.rc2;
-    f.sig2 = (float)c.sig2;
-    f.eps24 = (float)c.eps24;
-    f.amp = (float)c.amp;
-    f.xim = (float)c.xim;
-    f.shear = (float)c.shear;
-    f.half_Lz = (float)c.half_Lz;
-    f.Lz = (float)c.Lz;
-    f.shear_Lz = (float)c.shear_Lz;
-    f.R02 = (float)c.R02;
-    f.fene_k = (float)c.fene_k;
-    f.mass = (float)c.mass;
-    f.bins_per_Lz = (float)c.bins_per_Lz;
-  }
+  fill_geom(s, box, shear_rate, rc, skin, p);
   s->s.prec = p->precision;
   cudaError_t e;
   if (cuda_stream) {
@@ -893,5 +919,240 @@ LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes) {
   CKS(read_dyn(s));
   return status_from_err(s, s->h_dyn->err);
 }
+
+}  // extern "C"
+
+// =================================================================== batches
+// Many independent boxes advanced by one graph launch: each member's steps
+// are recorded on its own capture stream, forked from and joined back into
+// one batch capture, so the graph holds one branch per member and the device
+// runs the members' kernels concurrently.  The kernels are the members' own,
+// so every member's trajectory is bit-identical to stepping it alone.
+struct le_batch {
+  size_t budget = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap = nullptr;
+  std::vector<le_sim *> members;
+  cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
+  std::vector<cudaEvent_t> events;
+  std::string err;
+};
+
+namespace {
+
+le_status bfail(le_batch *b, le_status st, const std::string &msg) {
+  if (b) b->err = msg;
+  return st;
+}
+
+void batch_drop_graphs(le_batch *b) {
+  if (b->exec_chunk) cudaGraphExecDestroy(b->exec_chunk);
+  if (b->exec_one) cudaGraphExecDestroy(b->exec_one);
+  b->exec_chunk = b->exec_one = nullptr;
+}
+
+le_status batch_capture(le_batch *b, int steps, cudaGraphExec_t *out) {
+  const size_t m = b->members.size();
+  while (b->events.size() < m + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bfail(b, LE_ERR_CUDA, "event creation failed");
+    b->events.push_back(e);
+  }
+  cudaError_t ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, cudaGetErrorString(ce));
+  cudaGraph_t graph = nullptr;
+  cudaStreamCaptureStatus cs;
+  ce = cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
+  if (ce == cudaSuccess) ce = cudaEventRecord(b->events[m], b->cap);  // fork point
+  for (size_t k = 0; k < m && ce == cudaSuccess; ++k) {
+    le_sim *s = b->members[k];
+    ce = cudaStreamWaitEvent(s->cap_main, b->events[m], 0);
+    if (ce == cudaSuccess) ce = record_steps(s, s->cap_main, graph, steps, nullptr);
+    if (ce == cudaSuccess) ce = cudaEventRecord(b->events[k], s->cap_main);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->events[k], 0);  // join
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(b->cap, &captured);
+  if (ce == cudaSuccess) ce = ee;
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(out, captured, 0);
+  if (captured) cudaGraphDestroy(captured);
+  if (ce != cudaSuccess)
+    return bfail(b, LE_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
+  return LE_OK;
+}
+
+le_status batch_run(le_batch *b, int64_t nsteps) {
+  if (!b->exec_one) {
+    le_status st = batch_capture(b, 1, &b->exec_one);
+    if (st != LE_OK) return st;
+  }
+  if (!b->exec_chunk) {
+    le_status st = batch_capture(b, kChunk, &b->exec_chunk);
+    if (st != LE_OK) return st;
+  }
+  int64_t left = nsteps;
+  cudaError_t ce = cudaSuccess;
+  while (ce == cudaSuccess && left >= kChunk) {
+    ce = cudaGraphLaunch(b->exec_chunk, b->stream);
+    left -= kChunk;
+  }
+  while (ce == cudaSuccess && left > 0) {
+    ce = cudaGraphLaunch(b->exec_one, b->stream);
+    --left;
+  }
+  for (le_sim *s : b->members) launch_fold(s->s, b->stream);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+  if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, cudaGetErrorString(ce));
+  return LE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+LE_API le_status le_estimate_device_bytes(const double box[3], double shear_rate, double rc,
+                                          double skin, const le_params *p, int64_t n,
+                                          int64_t nbonds, size_t *bytes) {
+  if (!box || !p || !bytes || n < 1 || n > kMaxParticles || nbonds < 0) return LE_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > 0.0) || !((rc + skin) < 0.5 * box[a])) return LE_ERR_INVALID_ARG;
+  le_sim *s = new (std::nothrow) le_sim;
+  if (!s) return LE_ERR_OOM;
+  fill_geom(s, box, shear_rate, rc, skin, p);
+  if (nbonds > 0) s->bonds.assign(2, 0);  // only "bonds exist" matters for the cell edge
+  Geom &g = s->s.g;
+  g.maxb = nbonds > 0 ? 2 : 0;
+  choose_cells(s);
+  const double V = g.L[0] * g.L[1] * g.L[2];
+  const double mean_nb = 4.18879020478639 * g.rl * g.rl * g.rl * (double)n / V;
+  const int maxnb = (int)std::ceil(mean_nb * 1.6) + 32;
+  s->dry_run = true;
+  le_status st = allocate(s, n, maxnb);
+  // the rollback snapshot holds one more buffer set
+  const size_t vb = vec_bytes(s->s.prec);
+  const size_t snap = (size_t)n * (4 * vb + (s->s.prec == 1 ? 16 : 0) + 16 + 4) + sizeof(Dyn);
+  *bytes = s->device_bytes + snap;
+  s->dry_run = false;
+  delete s;
+  return st;
+}
+
+LE_API le_status le_batch_create(size_t budget_bytes, void *cuda_stream, le_batch **out) {
+  if (!out) return LE_ERR_INVALID_ARG;
+  *out = nullptr;
+  le_batch *b = new (std::nothrow) le_batch;
+  if (!b) return LE_ERR_OOM;
+  b->budget = budget_bytes;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = true;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    le_batch_destroy(b);
+    return LE_ERR_CUDA;
+  }
+  *out = b;
+  return LE_OK;
+}
+
+LE_API le_status le_batch_add(le_batch *b, le_sim *s) {
+  if (!b || !s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return bfail(b, LE_ERR_STATE, "a member needs its particles first");
+  size_t used = 0;
+  for (le_sim *m : b->members) {
+    if (m == s) return bfail(b, LE_ERR_INVALID_ARG, "already a member");
+    used += m->device_bytes;
+  }
+  if (b->budget && used + s->device_bytes > b->budget)
+    return bfail(b, LE_ERR_OOM, "the batch memory budget is full");
+  b->members.push_back(s);
+  batch_drop_graphs(b);
+  return LE_OK;
+}
+
+LE_API le_status le_batch_remove(le_batch *b, le_sim *s) {
+  if (!b || !s) return LE_ERR_INVALID_ARG;
+  for (size_t k = 0; k < b->members.size(); ++k)
+    if (b->members[k] == s) {
+      b->members.erase(b->members.begin() + (long)k);
+      batch_drop_graphs(b);
+      return LE_OK;
+    }
+  return bfail(b, LE_ERR_INVALID_ARG, "not a member");
+}
+
+LE_API le_status le_batch_step(le_batch *b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LE_ERR_INVALID_ARG;
+  if (nsteps == 0 || b->members.empty()) return LE_OK;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    std::vector<int> cur0(b->members.size());
+    for (size_t k = 0; k < b->members.size(); ++k) {
+      le_sim *s = b->members[k];
+      le_status st = read_dyn(s);
+      if (st == LE_OK) st = take_snapshot(s);
+      if (st == LE_OK) st = sync(s);
+      if (st != LE_OK) return bfail(b, st, s->err);
+      cur0[k] = s->h_dyn->cur;
+    }
+    le_status st = batch_run(b, nsteps);
+    if (st != LE_OK) return st;
+    bool failed = false, grow = false;
+    le_status first = LE_OK;
+    std::string msg;
+    for (le_sim *s : b->members) {
+      st = read_dyn(s);
+      if (st != LE_OK) return bfail(b, st, s->err);
+      if (s->h_dyn->err) {
+        failed = true;
+        le_status e = status_from_err(s, s->h_dyn->err);
+        if (e == LE_ERR_CAPACITY) grow = true;
+        else if (first == LE_OK) {
+          first = e;
+          msg = s->err;
+        }
+      }
+    }
+    if (!failed) return LE_OK;
+    // roll every member back to the start of the call
+    std::vector<int> seen(b->members.size());
+    for (size_t k = 0; k < b->members.size(); ++k) seen[k] = b->members[k]->h_dyn->list_max;
+    for (size_t k = 0; k < b->members.size(); ++k) {
+      st = restore_snapshot(b->members[k], cur0[k]);
+      if (st != LE_OK) return bfail(b, st, b->members[k]->err);
+    }
+    if (first != LE_OK) return bfail(b, first, msg + " (all members rolled back)");
+    if (!grow) break;
+    for (size_t k = 0; k < b->members.size(); ++k) {
+      le_sim *s = b->members[k];
+      if (seen[k] > s->s.g.maxnb) {
+        st = grow_list(s, (int)std::ceil(seen[k] * 1.3) + 16);
+        if (st != LE_OK) return bfail(b, st, s->err);
+      }
+    }
+    batch_drop_graphs(b);
+  }
+  return bfail(b, LE_ERR_CAPACITY, "neighbour list capacity could not be grown enough");
+}
+
+LE_API le_status le_batch_destroy(le_batch *b) {
+  if (!b) return LE_ERR_INVALID_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graphs(b);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LE_OK;
+}
+
+LE_API const char *le_batch_last_error(const le_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"
