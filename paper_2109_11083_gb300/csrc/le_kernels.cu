@@ -928,27 +928,23 @@ __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restric
           const bool self_slot = (slot == slot_code(0, 0, 0, 0));
           const uint32_t tag = (uint32_t)slot << kIndexBits;
           int j = j0;
-          for (; j + 1 < j1; j += 2) {
+          auto emit = [&](int jj, const float4 &q) {
+            const float dx = ax - q.x, dy = ay - q.y, dz = az - q.z;
+            if (dx * dx + dy * dy + dz * dz < rl2 && !(self_slot && jj == i)) {
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)jj | tag;
+              ++cnt;
+            }
+          };
+          // four candidates per pass: their loads are in flight together
+          for (; j + 3 < j1; j += 4) {
             const float4 qa = __ldg(b.pb + j), qb = __ldg(b.pb + j + 1);
-            const float dxa = ax - qa.x, dya = ay - qa.y, dza = az - qa.z;
-            const float dxb = ax - qb.x, dyb = ay - qb.y, dzb = az - qb.z;
-            if (dxa * dxa + dya * dya + dza * dza < rl2 && !(self_slot && j == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)j | tag;
-              ++cnt;
-            }
-            if (dxb * dxb + dyb * dyb + dzb * dzb < rl2 && !(self_slot && j + 1 == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)(j + 1) | tag;
-              ++cnt;
-            }
+            const float4 qc = __ldg(b.pb + j + 2), qd = __ldg(b.pb + j + 3);
+            emit(j, qa);
+            emit(j + 1, qb);
+            emit(j + 2, qc);
+            emit(j + 3, qd);
           }
-          if (j < j1) {
-            const float4 qa = __ldg(b.pb + j);
-            const float dxa = ax - qa.x, dya = ay - qa.y, dza = az - qa.z;
-            if (dxa * dxa + dya * dya + dza * dza < rl2 && !(self_slot && j == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)j | tag;
-              ++cnt;
-            }
-          }
+          for (; j < j1; ++j) emit(j, __ldg(b.pb + j));
         }
       }
     }
