@@ -71,6 +71,7 @@ class Samples(C.Structure):
         ("epot", C.c_double),
         ("vx_sum", C.POINTER(C.c_double)),
         ("count", C.POINTER(C.c_int64)),
+        ("vy2_sum", C.POINTER(C.c_double)),
     ]
 
 
@@ -222,9 +223,11 @@ class State:
         self.zimg = np.zeros(self.n, dtype=np.int32)
         nb = p.nbins if nbins is None else nbins
         self.vx_sum = np.zeros(max(nb, 1))
+        self.vy2_sum = np.zeros(max(nb, 1))
         self.count = np.zeros(max(nb, 1), dtype=np.int64)
         self.samples = Samples()
         self.samples.vx_sum = _dp(self.vx_sum)
+        self.samples.vy2_sum = _dp(self.vy2_sum)
         self.samples.count = self.count.ctypes.data_as(C.POINTER(C.c_int64))
         W = np.zeros(9)
         e = np.zeros(1)
@@ -257,3 +260,15 @@ class State:
         """Mean lab-frame vx per z bin over the samples taken so far."""
         with np.errstate(invalid="ignore", divide="ignore"):
             return self.vx_sum / self.count
+
+    @property
+    def ty_profile(self) -> np.ndarray:
+        """T_y per z bin (Sec. 3.1): mean of m vy^2 over the samples."""
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return self.vy2_sum / self.count
+
+    def density_profile(self, nsamples: int) -> np.ndarray:
+        """Number density per z bin (Sec. 3.1): mean count / bin volume."""
+        nb = self.count.shape[0]
+        L = np.broadcast_to(np.asarray([self.p.L[0], self.p.L[1], self.p.L[2]]), (3,))
+        return self.count / (nsamples * L[0] * L[1] * L[2] / nb)

@@ -38,7 +38,9 @@ typedef struct {
     int    lj_shift;      /* 1: energy shift of Eq. 10 (forces unchanged) */
     double fene_k, fene_R0; /* FENE, Eq. 11 */
     double mass, kT, xi, dt;
-    int    thermostat;    /* 0: none, 1: Langevin on peculiar velocity (Eq. 5) */
+    int    thermostat;    /* 0: none, 1: Langevin on the peculiar velocity (Eq. 5),
+                             2: Langevin on the absolute velocity (the xi_abs
+                             variant of Sec. 2.2 and Fig. 3) */
     uint64_t seed, system;
     int    nbins;         /* velocity-profile bins along z */
 } ora_params;
@@ -444,7 +446,9 @@ void ora_force_error_bound(const ora_params *p, double dX, int64_t n, const doub
 
 /* ------------------------------------------------------------------------- */
 /* Eq. 5: total force = conservative - xi*m*(v - v_s(z) e_x) + random, the
- * friction acting on the peculiar velocity.  v is the half-step velocity. */
+ * friction acting on the peculiar velocity.  v is the half-step velocity.
+ * Thermostat 2 is the paper's comparison variant (Sec. 2.2): the same
+ * friction and noise, the friction acting on the absolute velocity v. */
 static void thermostat_force(const ora_params *p, int64_t step, int64_t n,
                              const double *pos, const double *vel,
                              const double *Fc, double *Ftot)
@@ -452,11 +456,11 @@ static void thermostat_force(const ora_params *p, int64_t step, int64_t n,
     double amp = sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
     for (int64_t i = 0; i < n; ++i) {
         for (int a = 0; a < 3; ++a) Ftot[3 * i + a] = Fc[3 * i + a];
-        if (p->thermostat != 1) continue;
+        if (p->thermostat != 1 && p->thermostat != 2) continue;
         double u[3];
         ora_noise(p, step, i, u);
-        double vpec[3] = {vel[3 * i] - ora_vs(p, pos[3 * i + 2]), vel[3 * i + 1],
-                          vel[3 * i + 2]};
+        double vs = p->thermostat == 1 ? ora_vs(p, pos[3 * i + 2]) : 0.0;
+        double vpec[3] = {vel[3 * i] - vs, vel[3 * i + 1], vel[3 * i + 2]};
         for (int a = 0; a < 3; ++a)
             Ftot[3 * i + a] += -p->xi * p->mass * vpec[a] + amp * u[a];
     }
@@ -482,6 +486,7 @@ typedef struct {
     double epot;             /* last potential energy */
     double *vx_sum;          /* nbins: sum of lab-frame vx */
     int64_t *count;          /* nbins */
+    double *vy2_sum;         /* nbins: sum of m vy^2 (T_y profile, Sec. 3.1); may be NULL */
 } ora_samples;
 
 static void sample(const ora_params *p, int64_t n, const double *pos,
@@ -503,6 +508,7 @@ static void sample(const ora_params *p, int64_t n, const double *pos,
             if (bin >= p->nbins) bin = p->nbins - 1;
             s->vx_sum[bin] += vel[3 * i];
             s->count[bin] += 1;
+            if (s->vy2_sum) s->vy2_sum[bin] += p->mass * vel[3 * i + 1] * vel[3 * i + 1];
         }
     }
     for (int a = 0; a < 9; ++a) s->stress[a] = -(K[a] + W[a]) / V;
