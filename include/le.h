@@ -70,7 +70,9 @@ typedef enum le_precision {
 
 typedef enum le_thermostat {
     LE_THERMO_NONE = 0,
-    LE_THERMO_PECULIAR = 1    /* Langevin on the peculiar velocity v - v_s(z) e_x (Eq. 5) */
+    LE_THERMO_PECULIAR = 1,   /* Langevin on the peculiar velocity v - v_s(z) e_x (Eq. 5) */
+    LE_THERMO_ABSOLUTE = 2    /* the comparison variant of Sec. 2.2 (Fig. 3, xi_abs): the same
+                                 friction and noise acting on the lab-frame velocity v */
 } le_thermostat;
 
 typedef struct le_params {
@@ -146,6 +148,20 @@ LE_API le_status le_stress(le_sim *s, double out9[9], double *xz_avg, int64_t *n
  * last reset (NaN for an empty bin), and the particle counts per bin.
  * nbins must equal params.profile_bins. */
 LE_API le_status le_velocity_profile(le_sim *s, int nbins, double *vx_mean, int64_t *counts);
+
+/* The z-profiles of Sec. 3.1 (Fig. 3) over the same samples and bins as
+ * le_velocity_profile (bin b = floor(z / Lz * nbins), z wrapped into [0, Lz),
+ * full-step velocities):
+ *   vx_mean[b]  mean lab-frame vx,
+ *   t_y[b]      mean m vy^2 (the temperature from the vorticity component,
+ *               which the shear flow does not carry),
+ *   density[b]  mean particle count / bin volume (Lx Ly Lz / nbins),
+ *   counts[b]   particle samples in the bin.
+ * Any output pointer may be NULL; host arrays of nbins entries, owned by the
+ * caller.  nbins must equal le_params.profile_bins (else
+ * LE_ERR_INVALID_ARG).  Empty bins give NaN means. */
+LE_API le_status le_profiles(le_sim *s, int nbins, double *vx_mean, double *t_y, double *density,
+                             int64_t *counts);
 
 /* Mean peculiar temperature (3N - 3 degrees of freedom) over the samples. */
 LE_API le_status le_temperature(le_sim *s, double *tpec_avg);

@@ -30,7 +30,7 @@ STATUS = {
     7: "LE_ERR_CAPACITY", 8: "LE_ERR_TIMEOUT", 9: "LE_ERR_STATE",
 }
 LE_FP64, LE_FP32 = 0, 1
-LE_THERMO_NONE, LE_THERMO_PECULIAR = 0, 1
+LE_THERMO_NONE, LE_THERMO_PECULIAR, LE_THERMO_ABSOLUTE = 0, 1, 2
 
 
 class LEError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
                 "le_positions": (C.c_int, [_P, _D, _D]),
                 "le_stress": (C.c_int, [_P, _D, _D, C.POINTER(C.c_int64)]),
                 "le_velocity_profile": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_int64)]),
+                "le_profiles": (C.c_int, [_P, C.c_int, _D, _D, _D, C.POINTER(C.c_int64)]),
                 "le_temperature": (C.c_int, [_P, _D]),
                 "le_reset_samples": (C.c_int, [_P]),
                 "le_get_counters": (C.c_int, [_P, C.POINTER(le_counters)]),
@@ -127,7 +128,7 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points this binding expects the library to export."""
     return ["le_default_params", "le_create", "le_set_bonds", "le_set_particles", "le_step",
             "le_step_profiled", "le_forces", "le_positions", "le_stress",
-            "le_velocity_profile", "le_temperature", "le_reset_samples", "le_get_counters",
+            "le_velocity_profile", "le_profiles", "le_temperature", "le_reset_samples", "le_get_counters",
             "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
             "le_status_string", "le_forces_noalloc", "le_estimate_device_bytes",
             "le_batch_create", "le_batch_add", "le_batch_remove", "le_batch_step",
@@ -227,6 +228,15 @@ def le_velocity_profile(h: int, nbins: int):
     _check(h, lib().le_velocity_profile(h, nbins, vx.ctypes.data_as(_D),
                                         cnt.ctypes.data_as(C.POINTER(C.c_int64))))
     return vx, cnt
+
+
+def le_profiles(h: int, nbins: int):
+    """(vx mean, T_y, density, counts) per z bin over the samples (Sec. 3.1)."""
+    vx, ty, rho = np.empty(nbins), np.empty(nbins), np.empty(nbins)
+    cnt = np.empty(nbins, dtype=np.int64)
+    _check(h, lib().le_profiles(h, nbins, vx.ctypes.data_as(_D), ty.ctypes.data_as(_D),
+                                rho.ctypes.data_as(_D), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+    return vx, ty, rho, cnt
 
 
 def le_temperature(h: int) -> float:
@@ -361,6 +371,10 @@ class Sim:
 
     def velocity_profile(self):
         return le_velocity_profile(self.h, self.params.profile_bins)
+
+    def profiles(self):
+        """(vx mean, T_y, density, counts) per z bin (Sec. 3.1, Fig. 3)."""
+        return le_profiles(self.h, self.params.profile_bins)
 
     def temperature(self):
         return le_temperature(self.h)

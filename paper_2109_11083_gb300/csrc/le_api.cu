@@ -25,7 +25,7 @@ using namespace le;
 namespace {
 constexpr int kChunk = 16;
 constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
-constexpr int kStateVersion = 1;
+constexpr int kStateVersion = 2;
 }  // namespace
 
 struct le_sim {
@@ -187,8 +187,8 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   s->s.sort_blocks = (int)((n + kSortTile - 1) / kSortTile);
   CKS(dalloc(s, &w.hist, (size_t)kSortBuckets * s->s.sort_blocks));
   CKS(dalloc(s, &s->s.sort_part, sort_scan_parts(s->s.sort_blocks)));
-  CKS(dalloc(s, &w.acc_prof, 2 * (size_t)g.nbins));
-  CKS(dalloc(s, &w.sum_prof, (size_t)g.nbins));
+  CKS(dalloc(s, &w.acc_prof, 3 * (size_t)g.nbins));
+  CKS(dalloc(s, &w.sum_prof, 2 * (size_t)g.nbins));
   CKS(dalloc(s, &w.cnt_prof, (size_t)g.nbins));
   CKS(dalloc(s, &s->s.dyn, 1));
   CKS(dalloc(s, &s->s.stage, 6 * (size_t)n));
@@ -365,7 +365,7 @@ le_status take_snapshot(le_sim *s) {
     }
     for (int f = 0; f < 4; ++f) {  // dyn, sum_prof, cnt_prof, acc_prof
       void *q = nullptr;
-      CK(cudaMalloc(&q, std::max<size_t>(sizeof(Dyn) + 16 * (size_t)s->s.g.nbins, 256)));
+      CK(cudaMalloc(&q, std::max<size_t>(sizeof(Dyn) + 24 * (size_t)s->s.g.nbins, 256)));
       s->snap.push_back(q);
     }
   }
@@ -373,9 +373,9 @@ le_status take_snapshot(le_sim *s) {
     if (bytes[f]) CK(cudaMemcpyAsync(s->snap[f], ptr[f], bytes[f], cudaMemcpyDeviceToDevice, s->stream));
   const size_t nb = (size_t)s->s.g.nbins;
   CK(cudaMemcpyAsync(s->snap[7], s->s.dyn, sizeof(Dyn), cudaMemcpyDeviceToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->snap[8], s->s.w.sum_prof, 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->snap[8], s->s.w.sum_prof, 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
   CK(cudaMemcpyAsync(s->snap[9], s->s.w.cnt_prof, 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->snap[10], s->s.w.acc_prof, 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->snap[10], s->s.w.acc_prof, 24 * nb, cudaMemcpyDeviceToDevice, s->stream));
   return LE_OK;
 }
 
@@ -387,9 +387,9 @@ le_status restore_snapshot(le_sim *s, int cur) {
     if (bytes[f]) CK(cudaMemcpyAsync(ptr[f], s->snap[f], bytes[f], cudaMemcpyDeviceToDevice, s->stream));
   const size_t nb = (size_t)s->s.g.nbins;
   CK(cudaMemcpyAsync(s->s.dyn, s->snap[7], sizeof(Dyn), cudaMemcpyDeviceToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->s.w.sum_prof, s->snap[8], 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->s.w.sum_prof, s->snap[8], 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
   CK(cudaMemcpyAsync(s->s.w.cnt_prof, s->snap[9], 8 * nb, cudaMemcpyDeviceToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->s.w.acc_prof, s->snap[10], 16 * nb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->s.w.acc_prof, s->snap[10], 24 * nb, cudaMemcpyDeviceToDevice, s->stream));
   // the snapshot's cur names the set it was taken from
   int c = cur;
   CK(cudaMemcpyAsync(&s->s.dyn->cur, &c, sizeof(int), cudaMemcpyHostToDevice, s->stream));
@@ -405,8 +405,8 @@ le_status initialise(le_sim *s) {
   d.build_step = 0;
   d.cur = 0;
   CK(cudaMemcpyAsync(s->s.dyn, &d, sizeof(Dyn), cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 16 * (size_t)s->s.g.nbins, s->stream));
-  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 8 * (size_t)s->s.g.nbins, s->stream));
+  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 24 * (size_t)s->s.g.nbins, s->stream));
+  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 16 * (size_t)s->s.g.nbins, s->stream));
   CK(cudaMemsetAsync(s->s.w.cnt_prof, 0, 8 * (size_t)s->s.g.nbins, s->stream));
   launch_tables(s->s, s->stream);
   launch_import(s->s, s->stream);
@@ -474,7 +474,9 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
     return LE_ERR_INVALID_ARG;
   if (p->profile_bins < 1 || p->profile_bins > kMaxBins) return LE_ERR_INVALID_ARG;
   if (p->precision != LE_FP64 && p->precision != LE_FP32) return LE_ERR_INVALID_ARG;
-  if (p->thermostat != LE_THERMO_NONE && p->thermostat != LE_THERMO_PECULIAR) return LE_ERR_INVALID_ARG;
+  if (p->thermostat != LE_THERMO_NONE && p->thermostat != LE_THERMO_PECULIAR &&
+      p->thermostat != LE_THERMO_ABSOLUTE)
+    return LE_ERR_INVALID_ARG;
   const double rl = rc + skin;
   for (int a = 0; a < 3; ++a)
     if (!(rl < 0.5 * box[a])) return LE_ERR_BOX_TOO_SMALL;
@@ -803,6 +805,28 @@ LE_API le_status le_velocity_profile(le_sim *s, int nbins, double *vx_mean, int6
   return LE_OK;
 }
 
+LE_API le_status le_profiles(le_sim *s, int nbins, double *vx_mean, double *t_y, double *density,
+                             int64_t *counts) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  if (nbins != s->s.g.nbins) return fail(s, LE_ERR_INVALID_ARG, "nbins differs from profile_bins");
+  std::vector<double> sum(2 * (size_t)nbins);
+  std::vector<long long> cnt(nbins);
+  CK(cudaMemcpyAsync(sum.data(), s->s.w.sum_prof, 16 * (size_t)nbins, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(cnt.data(), s->s.w.cnt_prof, 8 * (size_t)nbins, cudaMemcpyDeviceToHost, s->stream));
+  CKS(read_dyn(s));
+  const Geom &g = s->s.g;
+  const double vbin = g.L[0] * g.L[1] * g.L[2] / nbins;
+  const long long ns = s->h_dyn->nsamples;
+  for (int b = 0; b < nbins; ++b) {
+    if (vx_mean) vx_mean[b] = cnt[b] ? sum[b] / (double)cnt[b] : NAN;
+    if (t_y) t_y[b] = cnt[b] ? sum[nbins + b] / (double)cnt[b] : NAN;
+    if (density) density[b] = ns ? (double)cnt[b] / ((double)ns * vbin) : NAN;
+    if (counts) counts[b] = cnt[b];
+  }
+  return LE_OK;
+}
+
 LE_API le_status le_reset_samples(le_sim *s) {
   if (!s) return LE_ERR_INVALID_ARG;
   if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
@@ -814,8 +838,8 @@ LE_API le_status le_reset_samples(le_sim *s) {
   d.pending = 0;
   CK(cudaMemcpyAsync(s->s.dyn, &d, sizeof(Dyn), cudaMemcpyHostToDevice, s->stream));
   const size_t nb = (size_t)s->s.g.nbins;
-  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 16 * nb, s->stream));
-  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 8 * nb, s->stream));
+  CK(cudaMemsetAsync(s->s.w.acc_prof, 0, 24 * nb, s->stream));
+  CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 16 * nb, s->stream));
   CK(cudaMemsetAsync(s->s.w.cnt_prof, 0, 8 * nb, s->stream));
   return sync(s);
 }
@@ -855,7 +879,7 @@ LE_API le_status le_get_state(le_sim *s, void *buf, size_t *bytes) {
   size_t fb[7];
   set_fields(s, s->h_dyn->cur, ptr, fb);
   const size_t nb = (size_t)s->s.g.nbins;
-  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 8 * nb + 8 * nb + 16 * nb;
+  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 16 * nb + 8 * nb + 24 * nb;
   for (int f = 0; f < 7; ++f) total += fb[f];
   if (!buf) {
     *bytes = total;
@@ -872,11 +896,11 @@ LE_API le_status le_get_state(le_sim *s, void *buf, size_t *bytes) {
     if (fb[f]) CK(cudaMemcpyAsync(o, ptr[f], fb[f], cudaMemcpyDeviceToHost, s->stream));
     o += fb[f];
   }
-  CK(cudaMemcpyAsync(o, s->s.w.sum_prof, 8 * nb, cudaMemcpyDeviceToHost, s->stream));
-  o += 8 * nb;
+  CK(cudaMemcpyAsync(o, s->s.w.sum_prof, 16 * nb, cudaMemcpyDeviceToHost, s->stream));
+  o += 16 * nb;
   CK(cudaMemcpyAsync(o, s->s.w.cnt_prof, 8 * nb, cudaMemcpyDeviceToHost, s->stream));
   o += 8 * nb;
-  CK(cudaMemcpyAsync(o, s->s.w.acc_prof, 16 * nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(o, s->s.w.acc_prof, 24 * nb, cudaMemcpyDeviceToHost, s->stream));
   *bytes = total;
   return sync(s);
 }
@@ -894,7 +918,7 @@ LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes) {
   void *ptr[7];
   size_t fb[7];
   set_fields(s, 0, ptr, fb);
-  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 32 * nb;
+  size_t total = sizeof(StateHeader) + sizeof(Dyn) + 48 * nb;
   for (int f = 0; f < 7; ++f) total += fb[f];
   if (bytes < total) return fail(s, LE_ERR_INVALID_ARG, "state blob truncated");
   const char *o = static_cast<const char *>(buf) + sizeof h;
@@ -909,11 +933,11 @@ LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes) {
     if (fb[f]) CK(cudaMemcpy(ptr[f], o, fb[f], cudaMemcpyHostToDevice));
     o += fb[f];
   }
-  CK(cudaMemcpy(s->s.w.sum_prof, o, 8 * nb, cudaMemcpyHostToDevice));
-  o += 8 * nb;
+  CK(cudaMemcpy(s->s.w.sum_prof, o, 16 * nb, cudaMemcpyHostToDevice));
+  o += 16 * nb;
   CK(cudaMemcpy(s->s.w.cnt_prof, o, 8 * nb, cudaMemcpyHostToDevice));
   o += 8 * nb;
-  CK(cudaMemcpy(s->s.w.acc_prof, o, 16 * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->s.w.acc_prof, o, 24 * nb, cudaMemcpyHostToDevice));
   launch_relist(s->s, s->stream);
   CK(cudaGetLastError());
   CKS(read_dyn(s));

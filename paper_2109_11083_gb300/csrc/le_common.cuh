@@ -175,8 +175,8 @@ struct Work {
   double *Xs;              // [3n] FP64 build positions, sorted order (bonded systems)
   uint32_t *key[2], *val[2];  // radix-sort ping-pong buffers
   uint32_t *hist;          // radix-sort digit counts
-  long long *acc_prof;     // [2*nbins] per-step fixed-point vx sums and counts
-  double *sum_prof;        // [nbins] running vx sums
+  long long *acc_prof;     // [3*nbins] per-step fixed-point vx sums, counts, m vy^2 sums
+  double *sum_prof;        // [2*nbins] running vx sums, then m vy^2 sums
   long long *cnt_prof;     // [nbins] running counts
 };
 

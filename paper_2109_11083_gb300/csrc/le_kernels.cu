@@ -205,9 +205,11 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
   if (pending) {
     for (int b = t; b < g.nbins; b += blockDim.x) {
       w.sum_prof[b] += (double)w.acc_prof[b] * kInvFixP;
+      w.sum_prof[g.nbins + b] += (double)w.acc_prof[2 * g.nbins + b] * kInvFixP;
       w.cnt_prof[b] += w.acc_prof[g.nbins + b];
       w.acc_prof[b] = 0;
       w.acc_prof[g.nbins + b] = 0;
+      w.acc_prof[2 * g.nbins + b] = 0;
     }
   }
   __syncthreads();
@@ -298,9 +300,11 @@ __global__ void k_fold(Geom g, Dyn *__restrict__ d, Work w) {
   if (pending) {
     for (int b = t; b < g.nbins; b += blockDim.x) {
       w.sum_prof[b] += (double)w.acc_prof[b] * kInvFixP;
+      w.sum_prof[g.nbins + b] += (double)w.acc_prof[2 * g.nbins + b] * kInvFixP;
       w.cnt_prof[b] += w.acc_prof[g.nbins + b];
       w.acc_prof[b] = 0;
       w.acc_prof[g.nbins + b] = 0;
+      w.acc_prof[2 * g.nbins + b] = 0;
     }
   }
   __syncthreads();
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
   __shared__ double s_red[2][kForceWarps];
   __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
   __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
-  extern __shared__ long long s_prof[];  // [2 * nbins]
+  extern __shared__ long long s_prof[];  // [3 * nbins]: vx sums, counts, m vy^2 sums
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cur = d->cur;
   const long long n1 = d->step;
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
   G.s = R(d->s);
   const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
-    for (int b = t; b < 2 * g.nbins; b += blockDim.x) s_prof[b] = 0;
+    for (int b = t; b < 3 * g.nbins; b += blockDim.x) s_prof[b] = 0;
   if (lane == 0) {
     mbar_init(&s_bar[warp][0], 1);
     mbar_init(&s_bar[warp][1], 1);
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
 
   R sxz = R(0), ke = R(0);
   int bin = -1;
-  R vxw = R(0);
+  R vxw = R(0), vy2 = R(0);
   if (active) {
     if constexpr (BONDS) {
       const R R02 = K.R02, kf = K.fene_k;
@@ -544,12 +548,20 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     const R zu = pi.z + pi.w;  // unwrapped z (reference + displacement)
     const R vs = K.shear * (zu - K.half_Lz);
     R ftx = fx, fty = fy, ftz = fz;
-    if (g.thermostat == 1) {
+    if (g.thermostat != 0) {
+      // 1: friction on the peculiar velocity (Eq. 5); 2: on the absolute
+      // velocity (the comparison variant of Sec. 2.2), same noise.  Between
+      // builds a particle that crossed the top/bottom face is kept unwrapped,
+      // velocity jump not yet applied: v - v_s is the same either way, but the
+      // absolute friction must see the wrapped lab velocity v - nz shear Lz.
       R u[3];
       uniform3<R>(g, n1, b.gid[i], u);
       const R amp = K.amp;
       const R xm = K.xim;
-      ftx += -xm * (v.x - vs) + amp * u[0];
+      const R vf = g.thermostat == 1
+                       ? vs
+                       : (zu >= K.Lz ? K.shear_Lz : (zu < R(0) ? -K.shear_Lz : R(0)));
+      ftx += -xm * (v.x - vf) + amp * u[0];
       fty += -xm * v.y + amp * u[1];
       ftz += -xm * v.z + amp * u[2];
     }
@@ -583,6 +595,7 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
       int bb = (int)floor(zw / Lz * R(g.nbins));
       bin = bb < 0 ? 0 : (bb >= g.nbins ? g.nbins - 1 : bb);
       vxw = vw;
+      vy2 = m * nv.y * nv.y;  // T_y profile (Sec. 3.1)
     }
   }
   if (!sample) return;
@@ -598,6 +611,8 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     // bin and warp (integer sums, so the order of addition does not matter)
     const float vc = fminf(fmaxf((float)vxw, -1000.f), 1000.f);
     const int q = bin >= 0 ? __float2int_rn(vc * (float)kFixP) : 0;
+    const float yc = fminf(fmaxf((float)vy2, 0.f), 2000.f);
+    const int qy = bin >= 0 ? __float2int_rn(yc * (float)kFixP) : 0;
     unsigned todo = __ballot_sync(0xffffffffu, bin >= 0);
     while (todo) {
       const int leader = __ffs(todo) - 1;
@@ -606,10 +621,14 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
       // split the 2^20 fixed-point values so 32 of them cannot overflow int32
       const int hi = __reduce_add_sync(0xffffffffu, bin == b0 ? (q >> 10) : 0);
       const int lo = __reduce_add_sync(0xffffffffu, bin == b0 ? (q & 1023) : 0);
+      const int yhi = __reduce_add_sync(0xffffffffu, bin == b0 ? (qy >> 10) : 0);
+      const int ylo = __reduce_add_sync(0xffffffffu, bin == b0 ? (qy & 1023) : 0);
       if (lane == leader) {
         atomicAdd((unsigned long long *)&s_prof[b0],
                   (unsigned long long)((long long)hi * 1024 + (long long)lo));
         atomicAdd((unsigned long long *)&s_prof[g.nbins + b0], (unsigned long long)__popc(grp));
+        atomicAdd((unsigned long long *)&s_prof[2 * g.nbins + b0],
+                  (unsigned long long)((long long)yhi * 1024 + (long long)ylo));
       }
       todo &= ~grp;
     }
@@ -630,6 +649,8 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     if (cn) {
       atomicAdd((unsigned long long *)&w.acc_prof[q], (unsigned long long)s_prof[q]);
       atomicAdd((unsigned long long *)&w.acc_prof[g.nbins + q], (unsigned long long)cn);
+      atomicAdd((unsigned long long *)&w.acc_prof[2 * g.nbins + q],
+                (unsigned long long)s_prof[2 * g.nbins + q]);
     }
   }
 }
@@ -1165,7 +1186,7 @@ void launch_fold(const SysDev &s, cudaStream_t st) { k_fold<<<1, 256, 0, st>>>(s
 
 void launch_force(const SysDev &s, int mode, cudaStream_t st) {
   const int nb = blocks_for(s.g.n, kForceThreads);
-  const size_t smem = sizeof(long long) * 2 * (size_t)s.g.nbins;
+  const size_t smem = sizeof(long long) * 3 * (size_t)s.g.nbins;
   const bool bonds = s.g.maxb > 0;
 #define FN(R, A, B)                                                                  \
   do {                                                                               \

@@ -200,8 +200,8 @@ size_t carve(SysDev &s, unsigned char *base, int64_t n) {
   s.sort_passes = sort_passes_for(g.sort_bits);
   w.hist = cv.take<uint32_t>((size_t)kSortBuckets * s.sort_blocks);
   s.sort_part = cv.take<uint32_t>(sort_scan_parts(s.sort_blocks));
-  w.acc_prof = cv.take<long long>(2);
-  w.sum_prof = cv.take<double>(1);
+  w.acc_prof = cv.take<long long>(3);
+  w.sum_prof = cv.take<double>(2);
   w.cnt_prof = cv.take<long long>(1);
   s.stage = cv.take<double>(6 * (size_t)n);
   s.partials = cv.take<double>(16);
@@ -255,7 +255,7 @@ extern "C" LE_API le_status le_forces_noalloc(const double box[3], double shear_
     d.s = f;
     d.cur = 0;
     cudaError_t e = cudaMemcpyAsync(s.dyn, &d, sizeof d, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.w.acc_prof, 0, 2 * sizeof(long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.w.acc_prof, 0, 3 * sizeof(long long), st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(s.stage, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.stage + 3 * n, 0, sizeof(double) * 3 * n, st);
