@@ -238,6 +238,9 @@ def run_ours(args):
     if args.eager:
         sim.set_eager(True)
     sim.step(args.warmup)
+    # launch shapes from the autotuner (trial steps are rolled back: the
+    # state and every later result are the same as without it)
+    tuned = None if args.eager else sim.tune(32)
     c0 = sim.counters()
 
     def barrier():
@@ -308,7 +311,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(w), parallelism="replicas" if world > 1 else "single"),
+            "config": dict(workload_config(w), parallelism="replicas" if world > 1 else "single",
+                           launch_shapes=({"force_threads": tuned[0], "list_threads": tuned[1],
+                                           "chosen_by": "autotuner (le_tune), trials rolled back"}
+                                          if tuned else None)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "k_force (pair force + Langevin + kick + samples)",
@@ -350,6 +356,7 @@ def run_batched(args):
     total = sum(s["n"] for s in specs)
     plain = [make_box_sim(le, s) for s in specs]
     batched = [make_box_sim(le, s) for s in specs]
+    tuned = [make_box_sim(le, s) for s in specs]
     w = max(args.warmup, 3)
     for s in plain:
         s.step(w)
@@ -357,6 +364,18 @@ def run_batched(args):
     for s in batched:
         b.add(s)
     b.step(w)
+    # the same boxes once more, launch shapes picked by the autotuner on the
+    # whole batch (the trials are rolled back, so these members stay on the
+    # same trajectories)
+    bt = le.Batch()
+    for s in tuned:
+        bt.add(s)
+    bt.step(w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tf, tl, tms = bt.tune(32)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in plain:
@@ -366,12 +385,17 @@ def run_batched(args):
     t0 = time.perf_counter()
     b.step(args.steps)
     torch.cuda.synchronize()
+    t_untuned = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bt.step(args.steps)
+    torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     equal = True
     for k in range(0, len(specs), max(1, len(specs) // 16)):
         rp, vp = plain[k].positions()
-        rb, vb = batched[k].positions()
-        equal = equal and bool(np.array_equal(rp, rb) and np.array_equal(vp, vb))
+        for other in (batched[k], tuned[k]):
+            rb, vb = other.positions()
+            equal = equal and bool(np.array_equal(rp, rb) and np.array_equal(vp, vb))
     value = total * args.steps / t_batch
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": w, "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True,
@@ -383,10 +407,15 @@ def run_batched(args):
             "plain": {"value": total * args.steps / t_plain, "unit": UNIT,
                       "what": "each box stepped by its own le_step, one after another"},
             "batched_over_plain": t_plain / t_batch,
-            "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16}}
+            "autotune": {"force_threads": tf, "list_threads": tl, "seconds": t_tune,
+                         "trial_ms_per_step": tms,
+                         "untuned_value": total * args.steps / t_untuned},
+            "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16,
+                               "what": "plain vs batched and vs autotuned batched"}}
     print(json.dumps(line), flush=True)
     b.close()
-    for s in plain + batched:
+    bt.close()
+    for s in plain + batched + tuned:
         s.close()
     return 0
 

@@ -179,9 +179,32 @@ typedef struct le_counters {
     int64_t cells[3];         /* cell grid */
     double  dX;               /* current image offset */
     double  list_mean;        /* mean neighbour count of the last build */
+    int32_t force_threads;    /* launch shape of the pair kernel (threads per block) */
+    int32_t list_threads;     /* launch shape of the list build */
 } le_counters;
 
 LE_API le_status le_get_counters(le_sim *s, le_counters *out);
+
+/* Launch shapes.  The pair kernel sums each particle's forces in its own
+ * thread in list order, the list build is one thread per particle and every
+ * sample is a fixed-point integer sum, so the threads per block of these two
+ * kernels change no result (trajectories are bit-identical); they only
+ * change speed.
+ *
+ * le_set_launch: force_threads in {32, 64, ..., 256}, list_threads in
+ * {32, 64, ..., 256} (multiples of 32; else LE_ERR_INVALID_ARG).  Takes
+ * effect at the next step (captured graphs are dropped).
+ *
+ * le_tune: the autotuner.  Times every pair of force_threads in {128, 256}
+ * and list_threads in {64, 128, 256} on this system, over 2 x 16 steps of
+ * its own step graph each (list builds included: steps_per_trial >= 16 is
+ * rounded to whole 16-step chunks), restoring the state before and after
+ * every trial, and keeps the fastest.  The state after le_tune is the state
+ * before it.  best_force / best_list (nullable) receive the choice;
+ * ms_per_step (nullable) its measured time per step. */
+LE_API le_status le_set_launch(le_sim *s, int force_threads, int list_threads);
+LE_API le_status le_tune(le_sim *s, int steps_per_trial, int *best_force, int *best_list,
+                         double *ms_per_step);
 
 /* Checkpoint: an opaque copy of the whole dynamical state in the library's
  * internal (cell-sorted) layout: positions, velocities, forces, the integer
@@ -232,6 +255,15 @@ LE_API le_status le_batch_remove(le_batch *b, le_sim *s);
 /* Advances every member nsteps.  On a member's error every member is rolled
  * back to the start of the call (list overflows are grown and retried). */
 LE_API le_status le_batch_step(le_batch *b, int64_t nsteps);
+
+/* The autotuner for a batch: every candidate shape of le_tune, applied to all
+ * members, times the batch itself over 2 x 16-step chunks (as le_batch_step
+ * runs it: all members' kernels together), every member rolled back to its
+ * state before each trial; the fastest is kept.  Results are unchanged (see
+ * le_set_launch).  best_force / best_list / ms_per_step (nullable) receive
+ * the choice and its time per batch step. */
+LE_API le_status le_batch_tune(le_batch *b, int steps_per_trial, int *best_force, int *best_list,
+                               double *ms_per_step);
 LE_API le_status le_batch_destroy(le_batch *b);
 LE_API const char *le_batch_last_error(const le_batch *b);
 

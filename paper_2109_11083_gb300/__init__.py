@@ -56,7 +56,7 @@ class le_counters(C.Structure):
         ("step", C.c_int64), ("particles", C.c_int64), ("rebuilds", C.c_int64),
         ("image_rebuilds", C.c_int64), ("list_capacity", C.c_int64),
         ("list_max", C.c_int64), ("cells", C.c_int64 * 3), ("dX", C.c_double),
-        ("list_mean", C.c_double),
+        ("list_mean", C.c_double), ("force_threads", C.c_int32), ("list_threads", C.c_int32),
     ]
 
 
@@ -97,6 +97,9 @@ def lib():
                 "le_temperature": (C.c_int, [_P, _D]),
                 "le_reset_samples": (C.c_int, [_P]),
                 "le_get_counters": (C.c_int, [_P, C.POINTER(le_counters)]),
+                "le_set_launch": (C.c_int, [_P, C.c_int, C.c_int]),
+                "le_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
+                "le_batch_tune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
                 "le_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
                 "le_set_state": (C.c_int, [_P, _P, C.c_size_t]),
                 "le_set_eager": (C.c_int, [_P, C.c_int]),
@@ -129,6 +132,7 @@ def exported_symbols() -> list[str]:
     return ["le_default_params", "le_create", "le_set_bonds", "le_set_particles", "le_step",
             "le_step_profiled", "le_forces", "le_positions", "le_stress",
             "le_velocity_profile", "le_profiles", "le_temperature", "le_reset_samples", "le_get_counters",
+            "le_set_launch", "le_tune", "le_batch_tune",
             "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
             "le_status_string", "le_forces_noalloc", "le_estimate_device_bytes",
             "le_batch_create", "le_batch_add", "le_batch_remove", "le_batch_step",
@@ -254,7 +258,8 @@ def le_get_counters(h: int) -> dict:
     _check(h, lib().le_get_counters(h, C.byref(c)))
     return dict(step=c.step, particles=c.particles, rebuilds=c.rebuilds,
                 image_rebuilds=c.image_rebuilds, list_capacity=c.list_capacity,
-                list_max=c.list_max, cells=tuple(c.cells), dX=c.dX, list_mean=c.list_mean)
+                list_max=c.list_max, cells=tuple(c.cells), dX=c.dX, list_mean=c.list_mean,
+                force_threads=c.force_threads, list_threads=c.list_threads)
 
 
 def le_get_state(h: int) -> bytes:
@@ -322,6 +327,24 @@ def le_batch_step(b: int, nsteps: int) -> None:
     _bcheck(b, lib().le_batch_step(b, int(nsteps)))
 
 
+def le_batch_tune(b: int, steps_per_trial: int = 32):
+    """The batch autotuner: (force threads, list threads, ms per batch step)."""
+    f, l, ms = C.c_int(), C.c_int(), C.c_double()
+    _bcheck(b, lib().le_batch_tune(b, int(steps_per_trial), C.byref(f), C.byref(l), C.byref(ms)))
+    return f.value, l.value, ms.value
+
+
+def le_set_launch(h: int, force_threads: int, list_threads: int) -> None:
+    _check(h, lib().le_set_launch(h, int(force_threads), int(list_threads)))
+
+
+def le_tune(h: int, steps_per_trial: int = 32):
+    """The autotuner: (force threads, list threads, ms per step) it chose."""
+    f, l, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(h, lib().le_tune(h, int(steps_per_trial), C.byref(f), C.byref(l), C.byref(ms)))
+    return f.value, l.value, ms.value
+
+
 def le_batch_destroy(b: int) -> None:
     _bcheck(None, lib().le_batch_destroy(b))
 
@@ -385,6 +408,13 @@ class Sim:
     def counters(self):
         return le_get_counters(self.h)
 
+    def set_launch(self, force_threads: int, list_threads: int):
+        le_set_launch(self.h, force_threads, list_threads)
+
+    def tune(self, steps_per_trial: int = 32):
+        """Autotunes the launch shapes (results unchanged); returns the choice."""
+        return le_tune(self.h, steps_per_trial)
+
     def get_state(self):
         return le_get_state(self.h)
 
@@ -429,6 +459,11 @@ class Batch:
 
     def step(self, nsteps: int):
         le_batch_step(self.b, nsteps)
+
+    def tune(self, steps_per_trial: int = 32):
+        """Autotunes the members' launch shapes on the whole batch (results
+        unchanged); returns (force threads, list threads, ms per step)."""
+        return le_batch_tune(self.b, steps_per_trial)
 
     def close(self):
         if self.b:

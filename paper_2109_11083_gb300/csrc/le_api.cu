@@ -10,11 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/le.h"
@@ -858,6 +861,84 @@ LE_API le_status le_get_counters(le_sim *s, le_counters *out) {
   for (int a = 0; a < 3; ++a) out->cells[a] = s->s.g.nc[a];
   out->dX = s->h_dyn->dX;
   out->list_mean = (double)s->h_dyn->list_entries / (double)s->n;
+  out->force_threads = s->s.force_threads;
+  out->list_threads = s->s.list_threads;
+  return LE_OK;
+}
+
+static void drop_graphs(le_sim *s) {
+  if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
+  if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
+  s->exec_chunk = s->exec_one = nullptr;
+}
+
+LE_API le_status le_set_launch(le_sim *s, int force_threads, int list_threads) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  auto ok = [](int t, int mx) { return t >= 32 && t <= mx && t % 32 == 0; };
+  if (!ok(force_threads, kForceThreads) || !ok(list_threads, kListMaxThreads))
+    return fail(s, LE_ERR_INVALID_ARG, "launch shape: multiples of 32 up to 256 threads");
+  s->s.force_threads = force_threads;
+  s->s.list_threads = list_threads;
+  drop_graphs(s);
+  return LE_OK;
+}
+
+// The autotuner: every candidate shape runs the system's own step graph from
+// the same snapshot (one chunk to warm, then the timed chunks), and the state
+// is restored after each trial, so tuning leaves no trace but the choice.
+LE_API le_status le_tune(le_sim *s, int steps_per_trial, int *best_force, int *best_list,
+                         double *ms_per_step) {
+  if (!s) return LE_ERR_INVALID_ARG;
+  if (!s->has_particles) return fail(s, LE_ERR_STATE, "le_set_particles has not been called");
+  if (steps_per_trial < 1) return fail(s, LE_ERR_INVALID_ARG, "steps_per_trial < 1");
+  const int chunks = std::max(1, steps_per_trial / kChunk);
+  CKS(read_dyn(s));
+  const int cur0 = s->h_dyn->cur;
+  CKS(take_snapshot(s));
+  const int forces[2] = {128, 256}, lists[3] = {64, 128, 256};
+  int bf = s->s.force_threads, bl = s->s.list_threads;
+  double best = 0.0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  le_status st = LE_OK;
+  for (int a = 0; a < 2 && st == LE_OK; ++a)
+    for (int c = 0; c < 3 && st == LE_OK; ++c) {
+      s->s.force_threads = forces[a];
+      s->s.list_threads = lists[c];
+      drop_graphs(s);
+      st = ensure_graphs(s);
+      if (st != LE_OK) break;
+      CK(cudaGraphLaunch(s->exec_chunk, s->stream));
+      CK(cudaEventRecord(e0, s->stream));
+      for (int k = 0; k < chunks; ++k) CK(cudaGraphLaunch(s->exec_chunk, s->stream));
+      CK(cudaEventRecord(e1, s->stream));
+      CKS(read_dyn(s));
+      const int err = s->h_dyn->err;
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      CKS(restore_snapshot(s, cur0));
+      if (err) {
+        st = status_from_err(s, err);
+        break;
+      }
+      const double per = (double)ms / (double)(chunks * kChunk);
+      if (best == 0.0 || per < best) {
+        best = per;
+        bf = forces[a];
+        bl = lists[c];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->s.force_threads = bf;
+  s->s.list_threads = bl;
+  drop_graphs(s);
+  if (st != LE_OK) return st;
+  if (!s->eager) CKS(ensure_graphs(s));
+  if (best_force) *best_force = bf;
+  if (best_list) *best_list = bl;
+  if (ms_per_step) *ms_per_step = best;
   return LE_OK;
 }
 
@@ -1164,6 +1245,74 @@ LE_API le_status le_batch_step(le_batch *b, int64_t nsteps) {
     batch_drop_graphs(b);
   }
   return bfail(b, LE_ERR_CAPACITY, "neighbour list capacity could not be grown enough");
+}
+
+LE_API le_status le_batch_tune(le_batch *b, int steps_per_trial, int *best_force, int *best_list,
+                               double *ms_per_step) {
+  if (!b || steps_per_trial < 1) return LE_ERR_INVALID_ARG;
+  if (b->members.empty()) return LE_OK;
+  const int chunks = std::max(1, steps_per_trial / kChunk);
+  std::vector<int> cur0(b->members.size());
+  for (size_t k = 0; k < b->members.size(); ++k) {
+    le_sim *s = b->members[k];
+    le_status st = read_dyn(s);
+    if (st == LE_OK) st = take_snapshot(s);
+    if (st == LE_OK) st = sync(s);
+    if (st != LE_OK) return bfail(b, st, s->err);
+    cur0[k] = s->h_dyn->cur;
+  }
+  auto restore_all = [&]() -> le_status {
+    for (size_t k = 0; k < b->members.size(); ++k) {
+      le_status st = restore_snapshot(b->members[k], cur0[k]);
+      if (st != LE_OK) return bfail(b, st, b->members[k]->err);
+    }
+    return LE_OK;
+  };
+  auto apply = [&](int f, int l) {
+    for (le_sim *s : b->members) {
+      s->s.force_threads = f;
+      s->s.list_threads = l;
+      drop_graphs(s);
+    }
+    batch_drop_graphs(b);
+  };
+  const int forces[2] = {128, 256}, lists[3] = {64, 128, 256};
+  int bf = b->members[0]->s.force_threads, bl = b->members[0]->s.list_threads;
+  double best = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < 3; ++c) {
+      apply(forces[a], lists[c]);
+      le_status st = batch_run(b, kChunk);  // captures and warms
+      std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+      if (st == LE_OK) st = batch_run(b, (int64_t)chunks * kChunk);
+      const double secs =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      bool failed = st != LE_OK;
+      for (le_sim *s : b->members) {
+        if (read_dyn(s) != LE_OK || s->h_dyn->err) failed = true;
+      }
+      le_status rs = restore_all();
+      if (rs != LE_OK) return rs;
+      if (failed) {
+        apply(bf, bl);
+        return bfail(b, LE_ERR_CAPACITY, "a tuning trial failed (all members rolled back)");
+      }
+      const double per = secs * 1e3 / (double)(chunks * kChunk);
+      if (best == 0.0 || per < best) {
+        best = per;
+        bf = forces[a];
+        bl = lists[c];
+      }
+    }
+  apply(bf, bl);
+  // the step graphs of the chosen shape, so the next step does not pay for them
+  le_status st = batch_capture(b, 1, &b->exec_one);
+  if (st == LE_OK) st = batch_capture(b, kChunk, &b->exec_chunk);
+  if (st != LE_OK) return st;
+  if (best_force) *best_force = bf;
+  if (best_list) *best_list = bl;
+  if (ms_per_step) *ms_per_step = best;
+  return LE_OK;
 }
 
 LE_API le_status le_batch_destroy(le_batch *b) {

@@ -390,6 +390,11 @@ __device__ __forceinline__ void slot_offset<float>(uint32_t e, const SlotGeo<flo
   oz = dcz * G.lz;
 }
 
+// A per-particle sample value in 2^-30 fixed point (the scale is a power of
+// two, so only the final rounding to an integer is inexact).
+__device__ __forceinline__ long long to_fix(float x) { return __float2ll_rn(x * 1073741824.0f); }
+__device__ __forceinline__ long long to_fix(double x) { return llrint(x * kFix); }
+
 template <class R> __device__ __forceinline__ R recip(R x) { return R(1) / x; }
 // FP32 pair loop: hardware reciprocal (rcp.approx, within 1 ulp), covered by
 // the per-pair evaluation rounding allowed in the FP32 error bound
@@ -427,7 +432,7 @@ template <class R, bool BONDS>
 __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
-  __shared__ double s_red[2][kForceWarps];
+  __shared__ long long s_red[2][kForceWarps];
   __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
   __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
   extern __shared__ long long s_prof[];  // [3 * nbins]: vx sums, counts, m vy^2 sums
@@ -599,9 +604,11 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     }
   }
   if (!sample) return;
-  // deterministic block sums -> fixed-point integer atomics
-  double a = (double)warp_sum(sxz);
-  double c = (double)warp_sum(ke);
+  // each particle's contribution in 2^-30 fixed point, then integer sums:
+  // the same totals for any grouping of particles into warps, blocks or
+  // batches (launch shapes change no sample)
+  const long long a = warp_sum(to_fix(sxz));
+  const long long c = warp_sum(to_fix(ke));
   if (lane == 0) {
     s_red[0][warp] = a;
     s_red[1][warp] = c;
@@ -635,13 +642,13 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
   }
   __syncthreads();
   if (t == 0) {
-    double A = 0.0, B = 0.0;
-    for (int k = 0; k < kForceWarps; ++k) {
+    long long A = 0, B = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
       A += s_red[0][k];
       B += s_red[1][k];
     }
-    atomicAdd((unsigned long long *)&d->acc_sxz, (unsigned long long)llrint(A * kFix));
-    atomicAdd((unsigned long long *)&d->acc_ke, (unsigned long long)llrint(B * kFix));
+    atomicAdd((unsigned long long *)&d->acc_sxz, (unsigned long long)A);
+    atomicAdd((unsigned long long *)&d->acc_ke, (unsigned long long)B);
     if (blockIdx.x == 0) d->pending = 1;
   }
   for (int q = t; q < g.nbins; q += blockDim.x) {
@@ -899,7 +906,7 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // (f_build/lx decides whether the window reaches a 4th cell).  Rows and
 // cells whose box lies farther than rl from the particle are skipped.
 template <class R>
-__global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+__global__ void __launch_bounds__(kListMaxThreads, 4) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                          Bufs<R> s1, Work w, int target_cur) {
   __shared__ float s_offx[kNumSlots];
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
@@ -974,13 +981,13 @@ __global__ void __launch_bounds__(kListThreads) k_rb_list(Geom g, Dyn *__restric
     if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
   }
   // total list entries (for the mean list length), one atomic per block
-  __shared__ unsigned long long s_tot[kListThreads / 32];
+  __shared__ unsigned long long s_tot[kListMaxThreads / 32];
   const unsigned long long c = warp_sum((unsigned long long)cnt);
   if ((threadIdx.x & 31) == 0) s_tot[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int k = 0; k < kListThreads / 32; ++k) t += s_tot[k];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_tot[k];
     atomicAdd((unsigned long long *)&d->list_entries, t);
   }
 }
@@ -1185,15 +1192,15 @@ void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, int use_cond, 
 void launch_fold(const SysDev &s, cudaStream_t st) { k_fold<<<1, 256, 0, st>>>(s.g, s.dyn, s.w); }
 
 void launch_force(const SysDev &s, int mode, cudaStream_t st) {
-  const int nb = blocks_for(s.g.n, kForceThreads);
+  const int nb = blocks_for(s.g.n, s.force_threads);
   const size_t smem = sizeof(long long) * 3 * (size_t)s.g.nbins;
   const bool bonds = s.g.maxb > 0;
 #define FN(R, A, B)                                                                  \
   do {                                                                               \
     if (bonds)                                                                       \
-      k_force<R, true><<<nb, kForceThreads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode);  \
+      k_force<R, true><<<nb, s.force_threads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode);  \
     else                                                                             \
-      k_force<R, false><<<nb, kForceThreads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode); \
+      k_force<R, false><<<nb, s.force_threads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode); \
   } while (0)
   LE_DISPATCH(s, FN);
 #undef FN
@@ -1210,8 +1217,8 @@ static void rebuild_tail(const SysDev &s, cudaStream_t st) {
   LE_DISPATCH(s, FN);
 #undef FN
   k_rb_ranges<<<nb, 256, 0, st>>>(s.g, skey, s.w.cell_start);
-  const int nl = blocks_for(n, kListThreads);
-#define FN(R, A, B) k_rb_list<R><<<nl, kListThreads, 0, st>>>(s.g, s.dyn, A, B, s.w, 0)
+  const int nl = blocks_for(n, s.list_threads);
+#define FN(R, A, B) k_rb_list<R><<<nl, s.list_threads, 0, st>>>(s.g, s.dyn, A, B, s.w, 0)
   LE_DISPATCH(s, FN);
 #undef FN
   if (s.g.maxb > 0) {
@@ -1242,8 +1249,8 @@ void launch_relist(const SysDev &s, cudaStream_t st) {
   LE_DISPATCH(s, FN);
 #undef FN
   k_rb_ranges<<<nb, 256, 0, st>>>(s.g, s.w.key[0], s.w.cell_start);
-  const int nl = blocks_for(n, kListThreads);
-#define FN(R, A, B) k_rb_list<R><<<nl, kListThreads, 0, st>>>(s.g, s.dyn, A, B, s.w, 1)
+  const int nl = blocks_for(n, s.list_threads);
+#define FN(R, A, B) k_rb_list<R><<<nl, s.list_threads, 0, st>>>(s.g, s.dyn, A, B, s.w, 1)
   LE_DISPATCH(s, FN);
 #undef FN
   if (s.g.maxb > 0) {

@@ -7,8 +7,11 @@
 namespace le {
 
 constexpr int kDriftThreads = 256;
+// Largest block sizes of the pair and list kernels (static shared arrays and
+// launch bounds); the sizes a system launches with are SysDev::force_threads
+// and SysDev::list_threads, which the autotuner may lower.
 constexpr int kForceThreads = 256;
-constexpr int kListThreads = 128;
+constexpr int kListMaxThreads = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;   // keys per thread and sort tile
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -22,6 +25,8 @@ struct SysDev {
   Bufs<double> f64[2];
   Work w;
   int prec = 0;         // 0: FP64, 1: FP32
+  int force_threads = 256;  // pair-kernel block (multiple of 32, <= kForceThreads)
+  int list_threads = 128;   // list-build block (multiple of 32, <= kListMaxThreads)
   int sort_passes = 1;  // radix passes; the sorted keys end in buffer (sort_passes & 1)
   int sort_blocks = 1;
   uint32_t *sort_part = nullptr;  // chunk sums of the count-table scan
