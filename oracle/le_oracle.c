@@ -43,6 +43,7 @@ typedef struct {
                              variant of Sec. 2.2 and Fig. 3) */
     uint64_t seed, system;
     int    nbins;         /* velocity-profile bins along z */
+    double angle_k;       /* k_a of the bending term of Eq. 12 (0: none) */
 } ora_params;
 
 enum { ORA_OK = 0, ORA_BOND_BROKEN = 1, ORA_BOX_TOO_SMALL = 2, ORA_NONFINITE = 3 };
@@ -271,6 +272,68 @@ static void pair_visit(void *vctx, int64_t i, int64_t j)
  * FENE over the bond list.  W receives sum_{i<j} r_ij (x) F_ij (the virial
  * part of Eq. 15), epot the potential energy (Eq. 13 without the angle term).
  * Returns ORA_BOND_BROKEN if any bond reaches R0 (Eq. 11: +infinity). */
+/* Eq. 12, bending term of the Kremer-Grest chains.  As printed the formula
+ * is garbled (linear in the angle while called a cosine potential); read as
+ * the cosine potential with its equilibrium at the stated 180 degrees,
+ *   V(theta) = k_a (1 - cos(theta - pi)) = k_a (1 + cos theta),
+ * theta the angle at the middle bead between its two bonds (a straight chain
+ * is the minimum).  With a = r_i - r_j, c = r_k - r_j (LE minimum images)
+ * and cos theta = a.c / (|a||c|):
+ *   F_i = -k_a (c^ - cos theta a^) / |a|,  F_k = -k_a (a^ - cos theta c^) / |c|,
+ *   F_j = -(F_i + F_k);
+ * virial a (x) F_i + c (x) F_k.  The angles are every pair of bonds that
+ * share a bead (one per inner bead of a linear chain). */
+static void angle_forces(const ora_params *p, double dX, int64_t n, const double *pos,
+                         int64_t nbond, const int32_t *bonds, double *F, double W[9],
+                         double *epot)
+{
+    int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t b = 0; b < nbond; ++b) {
+        ++deg[bonds[2 * b] + 1];
+        ++deg[bonds[2 * b + 1] + 1];
+    }
+    for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *nb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * nbond + 1));
+    for (int64_t i = 0; i < n; ++i) fill[i] = deg[i];
+    for (int64_t b = 0; b < nbond; ++b) {
+        int64_t i = bonds[2 * b], j = bonds[2 * b + 1];
+        nb[fill[i]++] = j;
+        nb[fill[j]++] = i;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t u = deg[j]; u < deg[j + 1]; ++u)
+            for (int64_t v = u + 1; v < deg[j + 1]; ++v) {
+                int64_t i = nb[u], k = nb[v];
+                double a[3], c[3];
+                ora_min_image(p, dX, pos + 3 * i, pos + 3 * j, a);
+                ora_min_image(p, dX, pos + 3 * k, pos + 3 * j, c);
+                double la = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+                double lc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                double ah[3], ch[3];
+                for (int q = 0; q < 3; ++q) {
+                    ah[q] = a[q] / la;
+                    ch[q] = c[q] / lc;
+                }
+                double ct = ah[0] * ch[0] + ah[1] * ch[1] + ah[2] * ch[2];
+                double fi[3], fk[3];
+                for (int q = 0; q < 3; ++q) {
+                    fi[q] = -p->angle_k * (ch[q] - ct * ah[q]) / la;
+                    fk[q] = -p->angle_k * (ah[q] - ct * ch[q]) / lc;
+                    F[3 * i + q] += fi[q];
+                    F[3 * k + q] += fk[q];
+                    F[3 * j + q] -= fi[q] + fk[q];
+                }
+                for (int q = 0; q < 3; ++q)
+                    for (int r = 0; r < 3; ++r) W[3 * q + r] += a[q] * fi[r] + c[q] * fk[r];
+                *epot += p->angle_k * (1.0 + ct);
+            }
+    }
+    free(deg);
+    free(fill);
+    free(nb);
+}
+
 int ora_forces(const ora_params *p, double dX, int64_t n, const double *pos,
                int64_t nbond, const int32_t *bonds, int use_cells,
                double *F, double *W, double *epot)
@@ -296,6 +359,7 @@ int ora_forces(const ora_params *p, double dX, int64_t n, const double *pos,
         for (int a = 0; a < 3; ++a)
             for (int q = 0; q < 3; ++q) c.W[3 * a + q] += d[a] * fr * d[q];
     }
+    if (p->angle_k != 0.0 && nbond > 0) angle_forces(p, dX, n, pos, nbond, bonds, F, c.W, &c.epot);
     if (W) memcpy(W, c.W, sizeof c.W);
     if (epot) *epot = c.epot;
     return broken ? ORA_BOND_BROKEN : ORA_OK;

@@ -194,15 +194,18 @@ def test_fene_reports_a_broken_bond():
     assert st == oracle.BOND_BROKEN
 
 
-@pytest.mark.parametrize("with_bonds", [False, True])
+@pytest.mark.parametrize("with_bonds", [0, 1, 2])
 def test_virial_is_minus_the_shear_strain_derivative_of_the_energy(with_bonds):
     """Affine shear x -> x + e z maps every separation d to d + e d_z e_x,
     including pairs across the shear plane once dX -> dX + e Lz.  Hence
     sum_{i<j} d_z F_x = -dU/de: this pins the virial part of Eq. 15 and the
-    sign of the image offset together."""
+    sign of the image offset together.  with_bonds = 2 adds the bending term
+    of Eq. 12, whose three-body virial a (x) F_i + c (x) F_k is pinned the
+    same way."""
     if with_bonds:
         pos, box, bonds = kg_chains_small(seed=9, frac=0.15)
-        p = oracle.params(box, 0.2, 2 ** (1 / 6), fene_k=30.0, fene_R0=1.5, lj_shift=1)
+        p = oracle.params(box, 0.2, 2 ** (1 / 6), fene_k=30.0, fene_R0=1.5, lj_shift=1,
+                          angle_k=1.5 if with_bonds == 2 else 0.0)
     else:
         pos, box = jittered_lattice(500, 0.8442, seed=21, amp=0.1)
         bonds = None
