@@ -89,6 +89,9 @@ typedef struct le_params {
     uint64_t system_id;       /*   and counter (step, particle id, 0, 0)                       */
     int    sample_every;      /* >0: accumulate stress and profile every this many steps */
     int    profile_bins;      /* number of z bins of the velocity profile (1..1024) */
+    double angle_k;           /* k_a of the chain bending term (Eq. 12, read as
+                                 k_a (1 + cos theta), theta the angle at the middle
+                                 bead of two bonds); 0: none; used only with bonds */
 } le_params;
 
 /* Fills *p with defaults: eps = sigma = mass = kT = xi = 1, dt = 0.005,

@@ -265,6 +265,7 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
     c.shear_Lz = shear_rate * box[2];
     c.R02 = p->fene_R0 * p->fene_R0;
     c.fene_k = p->fene_k;
+    c.ang_k = p->angle_k;
     c.mass = p->mass;
     c.bins_per_Lz = p->profile_bins / box[2];
     KConst<float> &f = g.cf;
@@ -281,6 +282,7 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
     f.shear_Lz = (float)c.shear_Lz;
     f.R02 = (float)c.R02;
     f.fene_k = (float)c.fene_k;
+    f.ang_k = (float)c.ang_k;
     f.mass = (float)c.mass;
     f.bins_per_Lz = (float)c.bins_per_Lz;
   }

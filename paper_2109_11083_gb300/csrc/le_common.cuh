@@ -85,6 +85,7 @@ template <class R> struct KConst {
   R shear_Lz;     // shear rate * Lz (velocity jump)
   R R02;          // FENE R0^2
   R fene_k;
+  R ang_k;        // bending constant of Eq. 12 (0: none)
   R mass;
   R bins_per_Lz;  // nbins / Lz
 };

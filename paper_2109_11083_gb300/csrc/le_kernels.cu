@@ -547,6 +547,74 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
         fz += fr * dz;
         vir += tx * dz;
       }
+      if (K.ang_k != R(0)) {
+        // Eq. 12, read as k_a (1 + cos theta): every angle this particle is
+        // part of -- as the middle bead of two of its bonds, or as an end of
+        // two bonds of a neighbour -- gathered here, so no other thread writes
+        // this force.  Separations use each bond's own slot (the neighbour's
+        // for its bonds), so angles across the sheared face need no extra
+        // image arithmetic.
+        const R ka = K.ang_k;
+        auto sep = [&](const V4<R> &po, uint32_t e, R &ax, R &ay, R &az) {
+          const V4<R> pq = load4(b.p + (e & kIndexMask));
+          R ox, oy, oz;
+          slot_offset<R>(e, G, ox, oy, oz);
+          ax = (po.x - pq.x) + ox;
+          ay = (po.y - pq.y) + oy;
+          az = (po.z - pq.z) + oz;
+        };
+        // force on the end bead at a = r_end - r_mid, the other end at c
+        auto end_force = [&](R ax, R ay, R az, R cx, R cy, R cz, R &gx, R &gy, R &gz) {
+          const R ia = R(1) / sqrt(ax * ax + ay * ay + az * az);
+          const R ic = R(1) / sqrt(cx * cx + cy * cy + cz * cz);
+          ax *= ia;
+          ay *= ia;
+          az *= ia;
+          cx *= ic;
+          cy *= ic;
+          cz *= ic;
+          const R ct = ax * cx + ay * cy + az * cz;
+          gx = -ka * (cx - ct * ax) * ia;
+          gy = -ka * (cy - ct * ay) * ia;
+          gz = -ka * (cz - ct * az) * ia;
+        };
+        for (int u = 0; u < g.maxb; ++u) {
+          const uint32_t eu = w.bond_e[(size_t)i * g.maxb + u];
+          if (eu == kNoBond) break;
+          R ux, uy, uz;  // r_i - r_j for the bonded neighbour j
+          sep(pi, eu, ux, uy, uz);
+          for (int v = u + 1; v < g.maxb; ++v) {
+            const uint32_t ev = w.bond_e[(size_t)i * g.maxb + v];
+            if (ev == kNoBond) break;
+            R vx, vy, vz;
+            sep(pi, ev, vx, vy, vz);
+            // i in the middle: the ends sit at -u and -v from i
+            R ax, ay, az, cx, cy, cz;
+            end_force(-ux, -uy, -uz, -vx, -vy, -vz, ax, ay, az);
+            end_force(-vx, -vy, -vz, -ux, -uy, -uz, cx, cy, cz);
+            fx -= ax + cx;
+            fy -= ay + cy;
+            fz -= az + cz;
+          }
+          // i at an end: the angles in the middle of j, with j's other bonds
+          const int j = (int)(eu & kIndexMask);
+          const V4<R> pj = load4(b.p + j);
+          for (int q = 0; q < g.maxb; ++q) {
+            const uint32_t ek = w.bond_e[(size_t)j * g.maxb + q];
+            if (ek == kNoBond) break;
+            if ((int)(ek & kIndexMask) == i) continue;  // the bond back to i
+            R kx, ky, kz;  // r_j - r_k
+            sep(pj, ek, kx, ky, kz);
+            R ax, ay, az;
+            end_force(ux, uy, uz, -kx, -ky, -kz, ax, ay, az);
+            fx += ax;
+            fy += ay;
+            fz += az;
+            // the angle's virial a (x) F_end, once per angle (vir is halved)
+            vir += R(2) * ux * az;
+          }
+        }
+      }
     }
     // Eq. 5: friction on the peculiar velocity plus the random force
     const V4<R> v = b.v[i];
@@ -1148,6 +1216,64 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
         const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
         if (e == kNoBond) break;
         pair((int)(e & kIndexMask), (int)(e >> kIndexBits), true);
+      }
+      if (g.cd.ang_k != 0.0) {
+        // Eq. 12 (k_a (1 + cos theta)): the energy once per angle at its
+        // middle bead, the virial a (x) F_end at each end bead
+        const double ka = g.cd.ang_k;
+        auto sepd = [&](int o, uint32_t e, double dd[3]) {
+          double xo[3], xq[3];
+          int co[3], cq[3];
+          const int q = (int)(e & kIndexMask);
+          absolute_position<R>(g, b, o, xo);
+          absolute_position<R>(g, b, q, xq);
+          cell_coords(g, __float_as_int(b.pb[o].w), co[0], co[1], co[2]);
+          cell_coords(g, __float_as_int(b.pb[q].w), cq[0], cq[1], cq[2]);
+          const int slot = (int)(e >> kIndexBits);
+          for (int a = 0; a < 3; ++a)
+            dd[a] = ((xo[a] - ((double)co[a] + 0.5) * g.lc[a]) -
+                     (xq[a] - ((double)cq[a] + 0.5) * g.lc[a])) + s_off[slot][a];
+        };
+        auto cosang = [](const double a[3], const double c[3], double ah[3], double ch[3],
+                         double &la) {
+          la = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+          const double lc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+          for (int k = 0; k < 3; ++k) {
+            ah[k] = a[k] / la;
+            ch[k] = c[k] / lc;
+          }
+          return ah[0] * ch[0] + ah[1] * ch[1] + ah[2] * ch[2];
+        };
+        for (int u = 0; u < g.maxb; ++u) {
+          const uint32_t eu = w.bond_e[(size_t)i * g.maxb + u];
+          if (eu == kNoBond) break;
+          double du[3];
+          sepd(i, eu, du);
+          for (int v = u + 1; v < g.maxb; ++v) {
+            const uint32_t ev = w.bond_e[(size_t)i * g.maxb + v];
+            if (ev == kNoBond) break;
+            double dv[3], a[3], c[3], ah[3], ch[3], la;
+            sepd(i, ev, dv);
+            for (int k = 0; k < 3; ++k) {
+              a[k] = -du[k];
+              c[k] = -dv[k];
+            }
+            acc[9] += ka * (1.0 + cosang(a, c, ah, ch, la));
+          }
+          const int j = (int)(eu & kIndexMask);
+          for (int q = 0; q < g.maxb; ++q) {
+            const uint32_t ek = w.bond_e[(size_t)j * g.maxb + q];
+            if (ek == kNoBond) break;
+            if ((int)(ek & kIndexMask) == i) continue;
+            double dk[3], c[3], ah[3], ch[3], la;
+            sepd(j, ek, dk);
+            for (int k = 0; k < 3; ++k) c[k] = -dk[k];
+            const double ct = cosang(du, c, ah, ch, la);
+            for (int a = 0; a < 3; ++a)
+              for (int cc = 0; cc < 3; ++cc)
+                acc[3 * a + cc] += du[a] * (-ka * (ch[cc] - ct * ah[cc]) / la);
+          }
+        }
       }
     }
     const V4<R> v = b.v[i];

@@ -118,6 +118,7 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   c.shear_Lz = shear_rate * box[2];
   c.R02 = p->fene_R0 * p->fene_R0;
   c.fene_k = p->fene_k;
+  c.ang_k = 0.0;  // no bonds here
   c.mass = p->mass;
   c.bins_per_Lz = 1.0 / box[2];
   KConst<float> &f = g.cf;
@@ -134,6 +135,7 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   f.shear_Lz = (float)c.shear_Lz;
   f.R02 = (float)c.R02;
   f.fene_k = (float)c.fene_k;
+  f.ang_k = 0.f;
   f.mass = (float)c.mass;
   f.bins_per_Lz = (float)c.bins_per_Lz;
   // cell grid of edge >= rc + skin
