@@ -28,7 +28,7 @@ using namespace le;
 namespace {
 constexpr int kChunk = 16;
 constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
-constexpr int kStateVersion = 2;
+constexpr int kStateVersion = 3;
 }  // namespace
 
 struct le_sim {

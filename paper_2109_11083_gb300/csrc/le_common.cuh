@@ -125,6 +125,7 @@ struct Dyn {
   double dX_build;       // dX(build_step)
   double f_build;        // dX(build_step) - m_build * lx, in [0, lx)
   double s;              // continuous cross-face shift of this step
+  float s_f;             // s rounded to float (FP32 pair kernel)
   float f_hi, f_lo;      // f_build as an unevaluated float sum (FP32 re-basing)
   int m_build;
   int win_lo[2], win_hi[2];  // x-cell window of rows across the top/bottom face, [dcz=-1, dcz=+1]

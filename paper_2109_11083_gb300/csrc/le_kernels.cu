@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
       s = d->f_build + ds;
     }
     d->s = s;
+    d->s_f = (float)s;
     d->dX = dX1;
     d->step = n1;
     d->rebuild = need ? 1 : 0;
@@ -398,12 +399,16 @@ __device__ __forceinline__ long long to_fix(double x) { return llrint(x * kFix);
 template <class R> __device__ __forceinline__ R recip(R x) { return R(1) / x; }
 // FP32 pair loop: hardware reciprocal (rcp.approx, within 1 ulp), covered by
 // the per-pair evaluation rounding allowed in the FP32 error bound
-template <> __device__ __forceinline__ float recip<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ float recip<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 template <class R>
 __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
-                                        const SlotGeo<R> &G, R rc2, R sig2, R eps24, R &fx,
-                                        R &fy, R &fz, R &vir) {
+                                        const SlotGeo<R> &G, R rc2, R sig2, R eps24, R eps48,
+                                        R &fx, R &fy, R &fz, R &vir) {
   R ox, oy, oz;
   slot_offset<R>(e, G, ox, oy, oz);
   const R dx = (pi.x - pj.x) + ox;
@@ -416,7 +421,8 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   const R ir2 = recip<R>(in ? r2 : R(1));
   const R s2 = sig2 * ir2;
   const R s6 = s2 * s2 * s2;
-  const R fr = in ? eps24 * ir2 * s6 * (R(2) * s6 - R(1)) : R(0);
+  // 24 eps (2 s^12 - s^6) / r^2
+  const R fr = in ? ir2 * s6 * fma(eps48, s6, -eps24) : R(0);
   const R tx = fr * dx;
   fx += tx;
   fy += fr * dy;
@@ -439,11 +445,20 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cur = d->cur;
   const long long n1 = d->step;
+  // cell edges and cross-face shift in the kernel's precision (the FP32
+  // kernel reads float copies: no FP64 conversion per thread)
   SlotGeo<R> G;
-  G.lx = R(g.lc[0]);
-  G.ly = R(g.lc[1]);
-  G.lz = R(g.lc[2]);
-  G.s = R(d->s);
+  if constexpr (sizeof(R) == 4) {
+    G.lx = g.lc_hi[0];
+    G.ly = g.lc_hi[1];
+    G.lz = g.lc_hi[2];
+    G.s = d->s_f;
+  } else {
+    G.lx = g.lc[0];
+    G.ly = g.lc[1];
+    G.lz = g.lc[2];
+    G.s = d->s;
+  }
   const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
     for (int b = t; b < 3 * g.nbins; b += blockDim.x) s_prof[b] = 0;
@@ -473,7 +488,7 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
   if (lane == 0)
     for (int c = 0; c < min(2, nchunks); ++c) issue(c);
 
-  const R rc2 = K.rc2, sig2 = K.sig2, eps24 = K.eps24;
+  const R rc2 = K.rc2, sig2 = K.sig2, eps24 = K.eps24, eps48 = R(2) * K.eps24;
   R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
   V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
   if (active) pi = b.p[i];
@@ -496,15 +511,15 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
       const V4<R> q1 = load4(b.p + (e1 & kIndexMask));
       const V4<R> q2 = load4(b.p + (e2 & kIndexMask));
       const V4<R> q3 = load4(b.p + (e3 & kIndexMask));
-      lj_pair<R>(pi, q0, e0, G, rc2, sig2, eps24, fx, fy, fz, vir);
-      lj_pair<R>(pi, q1, e1, G, rc2, sig2, eps24, fx, fy, fz, vir);
-      lj_pair<R>(pi, q2, e2, G, rc2, sig2, eps24, fx, fy, fz, vir);
-      lj_pair<R>(pi, q3, e3, G, rc2, sig2, eps24, fx, fy, fz, vir);
+      lj_pair<R>(pi, q0, e0, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      lj_pair<R>(pi, q1, e1, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      lj_pair<R>(pi, q2, e2, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      lj_pair<R>(pi, q3, e3, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
     }
     for (; r < rn; ++r) {
       const uint32_t e = rows[r][lane];
       const V4<R> q = load4(b.p + (e & kIndexMask));
-      lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, fx, fy, fz, vir);
+      lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
     }
     __syncwarp();
     if (lane == 0 && c + 2 < nchunks) {

@@ -255,6 +255,7 @@ extern "C" LE_API le_status le_forces_noalloc(const double box[3], double shear_
     d.m_build = m;
     d.f_build = f;
     d.s = f;
+    d.s_f = (float)f;
     d.cur = 0;
     cudaError_t e = cudaMemcpyAsync(s.dyn, &d, sizeof d, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.w.acc_prof, 0, 3 * sizeof(long long), st);
