@@ -97,6 +97,8 @@ def lib():
             L.ora_philox4x64.argtypes = [C.POINTER(C.c_uint64)] * 3
             L.ora_noise.restype = None
             L.ora_noise.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, _D]
+            L.ora_pair_uniform.restype = C.c_double
+            L.ora_pair_uniform.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, C.c_int64]
             L.ora_forces.restype = C.c_int
             L.ora_forces.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
                                      C.c_int64, _I32, C.c_int, _D, _D, _D]
@@ -169,6 +171,18 @@ def noise(p: Params, step: int, gid: int) -> np.ndarray:
     u = np.zeros(3)
     lib().ora_noise(C.byref(p), step, gid, _dp(u))
     return u
+
+
+def pair_uniform(p: Params, step: int, a: int, b: int) -> float:
+    """theta_ij of the DPD random force (Eq. 7): U(-1/2, 1/2), shared by a pair."""
+    return lib().ora_pair_uniform(C.byref(p), step, a, b)
+
+
+def thermostat_forces(p: Params, step: int, pos, vel, bonds=None):
+    """(Fc, Ftot) at step for the state (pos, half-step vel): Ftot includes the
+    thermostat (Eq. 5, its absolute variant, or DPD of Eqs. 6-8)."""
+    s = State(p, pos, vel, bonds=bonds, step=step)
+    return s.Fc.copy(), s.Ftot.copy()
 
 
 def forces(p: Params, dx_offset: float, pos, bonds=None, use_cells=True):

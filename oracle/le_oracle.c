@@ -40,7 +40,7 @@ typedef struct {
     double mass, kT, xi, dt;
     int    thermostat;    /* 0: none, 1: Langevin on the peculiar velocity (Eq. 5),
                              2: Langevin on the absolute velocity (the xi_abs
-                             variant of Sec. 2.2 and Fig. 3) */
+                             variant of Sec. 2.2 and Fig. 3), 3: DPD (Eqs. 6-8) */
     uint64_t seed, system;
     int    nbins;         /* velocity-profile bins along z */
     double angle_k;       /* k_a of the bending term of Eq. 12 (0: none) */
@@ -509,6 +509,61 @@ void ora_force_error_bound(const ora_params *p, double dX, int64_t n, const doub
 }
 
 /* ------------------------------------------------------------------------- */
+/* Eqs. 6-8, the DPD thermostat: pairwise dissipative and random forces for
+ * r < rc.  As printed both carry |r^.v_ij| and the random force has no
+ * 1/sqrt(dt); read as the textbook form that satisfies the fluctuation-
+ * dissipation relation with the paper's own noise pattern (Eq. 7's
+ * sqrt(24 kT xi) theta, theta in U(-1/2, 1/2)):
+ *   F_ij = [-xi w^2 (r^.v_ij) + sqrt(24 kT xi / dt) theta_ij w] r^,
+ *   w = 1 - r/rc (Eq. 8),  r^ = d/r,  d = the LE minimum image r_i - r_j.
+ * v_ij is the velocity of i relative to the image of j that d refers to:
+ * the image above the box (d_z shifted by -Lz) moves at +shear_rate*Lz
+ * along x, so v_ij = v_i - v_j - shear_rate*Lz e_x, mirrored below.
+ * theta_ij is shared by the two members of a pair: Philox4x64-10 with key
+ * (seed, system) and counter (step, min id, max id, 1) (the 1 separates it
+ * from the Langevin stream), first output word to U(-1/2, 1/2) by its top
+ * 53 bits.  F_ji = -F_ij exactly, so DPD conserves momentum. */
+double ora_pair_uniform(const ora_params *p, int64_t n, int64_t a, int64_t b)
+{
+    uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+    uint64_t ctr[4] = {(uint64_t)n, lo, hi, 1};
+    uint64_t key[2] = {p->seed, p->system};
+    uint64_t out[4];
+    ora_philox4x64(ctr, key, out);
+    return (double)(out[0] >> 11) * 0x1.0p-53 - 0.5;
+}
+
+typedef struct {
+    const ora_params *p;
+    double dX;
+    int64_t step;
+    const double *pos, *vel;
+    double *F;
+} dpd_ctx;
+
+static void dpd_visit(void *vctx, int64_t i, int64_t j)
+{
+    dpd_ctx *c = (dpd_ctx *)vctx;
+    const ora_params *p = c->p;
+    double d[3];
+    ora_min_image(p, c->dX, c->pos + 3 * i, c->pos + 3 * j, d);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < p->rc * p->rc)) return;
+    double r = sqrt(r2), w = 1.0 - r / p->rc;
+    double raw_dz = c->pos[3 * i + 2] - c->pos[3 * j + 2];
+    double vshift = 0.0;
+    if (raw_dz > 0.5 * p->L[2]) vshift = -p->shear_rate * p->L[2];
+    else if (raw_dz < -0.5 * p->L[2]) vshift = p->shear_rate * p->L[2];
+    double v[3] = {c->vel[3 * i] - c->vel[3 * j] + vshift,
+                   c->vel[3 * i + 1] - c->vel[3 * j + 1],
+                   c->vel[3 * i + 2] - c->vel[3 * j + 2]};
+    double ev = (d[0] * v[0] + d[1] * v[1] + d[2] * v[2]) / r;
+    double theta = ora_pair_uniform(p, c->step, i, j);
+    double f = -p->xi * w * w * ev + sqrt(24.0 * p->kT * p->xi / p->dt) * theta * w;
+    for (int a = 0; a < 3; ++a) c->F[3 * i + a] += f * d[a] / r;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Eq. 5: total force = conservative - xi*m*(v - v_s(z) e_x) + random, the
  * friction acting on the peculiar velocity.  v is the half-step velocity.
  * Thermostat 2 is the paper's comparison variant (Sec. 2.2): the same
@@ -518,6 +573,12 @@ static void thermostat_force(const ora_params *p, int64_t step, int64_t n,
                              const double *Fc, double *Ftot)
 {
     double amp = sqrt(24.0 * p->xi * p->kT * p->mass / p->dt);
+    if (p->thermostat == 3) {
+        memcpy(Ftot, Fc, sizeof(double) * 3 * n);
+        dpd_ctx c = {p, ora_dX(p, step), step, pos, vel, Ftot};
+        for_candidates(p, n, pos, 1, &c, dpd_visit);
+        return;
+    }
     for (int64_t i = 0; i < n; ++i) {
         for (int a = 0; a < 3; ++a) Ftot[3 * i + a] = Fc[3 * i + a];
         if (p->thermostat != 1 && p->thermostat != 2) continue;
