@@ -71,8 +71,14 @@ typedef enum le_precision {
 typedef enum le_thermostat {
     LE_THERMO_NONE = 0,
     LE_THERMO_PECULIAR = 1,   /* Langevin on the peculiar velocity v - v_s(z) e_x (Eq. 5) */
-    LE_THERMO_ABSOLUTE = 2    /* the comparison variant of Sec. 2.2 (Fig. 3, xi_abs): the same
+    LE_THERMO_ABSOLUTE = 2,   /* the comparison variant of Sec. 2.2 (Fig. 3, xi_abs): the same
                                  friction and noise acting on the lab-frame velocity v */
+    LE_THERMO_DPD = 3         /* DPD (Eqs. 6-8, read as the fluctuation-dissipation form):
+                                 F_ij = [-xi w^2 (r^.v_ij) + sqrt(24 kT xi/dt) theta_ij w] r^,
+                                 w = 1 - r/rc, for every pair within rc, v_ij against the
+                                 image j refers to (moving at +-shear_rate*Lz across the
+                                 face), theta_ij in U(-1/2,1/2) from Philox4x64-10 at counter
+                                 (step, min id, max id, 1); momentum-conserving */
 } le_thermostat;
 
 typedef struct le_params {

@@ -30,7 +30,7 @@ STATUS = {
     7: "LE_ERR_CAPACITY", 8: "LE_ERR_TIMEOUT", 9: "LE_ERR_STATE",
 }
 LE_FP64, LE_FP32 = 0, 1
-LE_THERMO_NONE, LE_THERMO_PECULIAR, LE_THERMO_ABSOLUTE = 0, 1, 2
+LE_THERMO_NONE, LE_THERMO_PECULIAR, LE_THERMO_ABSOLUTE, LE_THERMO_DPD = 0, 1, 2, 3
 
 
 class LEError(RuntimeError):

@@ -183,6 +183,8 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   CKS(dalloc(s, (char **)&w.tmp_p, (size_t)n * vb));
   if (prec == 1) CKS(dalloc(s, &w.tmp_lo, n));
   CKS(dalloc(s, &w.Xs, 3 * (size_t)n));
+  w.vnew = nullptr;
+  if (g.thermostat == LE_THERMO_DPD) CKS(dalloc(s, (char **)&w.vnew, (size_t)n * vb));
   for (int k = 0; k < 2; ++k) {
     CKS(dalloc(s, &w.key[k], n));
     CKS(dalloc(s, &w.val[k], n));
@@ -266,6 +268,9 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
     c.R02 = p->fene_R0 * p->fene_R0;
     c.fene_k = p->fene_k;
     c.ang_k = p->angle_k;
+    c.dpd_xi = p->xi;
+    c.dpd_amp = std::sqrt(24.0 * p->kT * p->xi / p->dt);
+    c.inv_rc = 1.0 / rc;
     c.mass = p->mass;
     c.bins_per_Lz = p->profile_bins / box[2];
     KConst<float> &f = g.cf;
@@ -283,6 +288,9 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
     f.R02 = (float)c.R02;
     f.fene_k = (float)c.fene_k;
     f.ang_k = (float)c.ang_k;
+    f.dpd_xi = (float)c.dpd_xi;
+    f.dpd_amp = (float)c.dpd_amp;
+    f.inv_rc = (float)c.inv_rc;
     f.mass = (float)c.mass;
     f.bins_per_Lz = (float)c.bins_per_Lz;
   }
@@ -479,9 +487,7 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
     return LE_ERR_INVALID_ARG;
   if (p->profile_bins < 1 || p->profile_bins > kMaxBins) return LE_ERR_INVALID_ARG;
   if (p->precision != LE_FP64 && p->precision != LE_FP32) return LE_ERR_INVALID_ARG;
-  if (p->thermostat != LE_THERMO_NONE && p->thermostat != LE_THERMO_PECULIAR &&
-      p->thermostat != LE_THERMO_ABSOLUTE)
-    return LE_ERR_INVALID_ARG;
+  if (p->thermostat < LE_THERMO_NONE || p->thermostat > LE_THERMO_DPD) return LE_ERR_INVALID_ARG;
   const double rl = rc + skin;
   for (int a = 0; a < 3; ++a)
     if (!(rl < 0.5 * box[a])) return LE_ERR_BOX_TOO_SMALL;

@@ -86,6 +86,9 @@ template <class R> struct KConst {
   R R02;          // FENE R0^2
   R fene_k;
   R ang_k;        // bending constant of Eq. 12 (0: none)
+  R dpd_xi;       // DPD friction xi (Eq. 6)
+  R dpd_amp;      // sqrt(24 kT xi / dt): DPD random-force amplitude (Eq. 7)
+  R inv_rc;       // 1 / rc (the DPD weight of Eq. 8)
   R mass;
   R bins_per_Lz;  // nbins / Lz
 };
@@ -175,6 +178,7 @@ struct Work {
   void *tmp_p;             // [n] re-based displacement (Vec<R>), pre-sort order
   float4 *tmp_lo;          // [n] FP32 mode: its low parts
   double *Xs;              // [3n] FP64 build positions, sorted order (bonded systems)
+  void *vnew;              // [n] DPD: kicked velocities (Vec<R>), copied back after the pair kernel
   uint32_t *key[2], *val[2];  // radix-sort ping-pong buffers
   uint32_t *hist;          // radix-sort digit counts
   long long *acc_prof;     // [3*nbins] per-step fixed-point vx sums, counts, m vy^2 sums
@@ -239,6 +243,20 @@ __device__ __forceinline__ void uniform3(const Geom &g, long long n, int gid, R 
     else
       u[k] = (float)(uint32_t)(c[k] >> 40) * 0x1.0p-24f - 0.5f;
   }
+}
+
+// DPD pair noise theta_ij (Eq. 7): shared by the two members of a pair,
+// counter (step, min id, max id, 1) -- the 1 keeps it apart from the
+// Langevin stream -- first output word mapped like uniform3.
+template <class R>
+__device__ __forceinline__ R pair_uniform(const Geom &g, long long n, int a, int b) {
+  const uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+  uint64_t c[4] = {(uint64_t)n, (uint64_t)lo, (uint64_t)hi, 1ull};
+  philox4x64_10(c, g.seed, g.system);
+  if constexpr (sizeof(R) == 8)
+    return (double)(c[0] >> 11) * 0x1.0p-53 - 0.5;
+  else
+    return (float)(uint32_t)(c[0] >> 40) * 0x1.0p-24f - 0.5f;
 }
 
 }  // namespace le

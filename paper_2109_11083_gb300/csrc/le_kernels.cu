@@ -430,12 +430,60 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   vir += tx * dz;
 }
 
+// DPD (Eqs. 6-8, read as the fluctuation-dissipation form): the dissipative
+// and random pair forces for r < rc, added to t (the thermostat part of the
+// total force, not the conservative force).  v_ij is taken against the image
+// of j the slot names: across the face that image moves at cz shear_rate Lz
+// (cz = dcz for a pair across the face, else 0), the time derivative of the
+// slot offset cz s(t).  Each thread evaluates its own side of a pair; the
+// shared theta_ij and the exact antisymmetry of d make F_ji = -F_ij.
+template <class R>
+__device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V4<R> &vi, int gi,
+                                         const Bufs<R> &b, uint32_t e, const SlotGeo<R> &G,
+                                         long long n1, R rc2, R &tx, R &ty, R &tz) {
+  const int j = (int)(e & kIndexMask);
+  const V4<R> pj = load4(b.p + j);
+  R ox, oy, oz;
+  slot_offset<R>(e, G, ox, oy, oz);
+  const R dx = (pi.x - pj.x) + ox;
+  const R dy = (pi.y - pj.y) + oy;
+  const R dz = (pi.z - pj.z) + oz;
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  if (!(r2 < rc2)) return;
+  const KConst<R> &K = kc<R>(g);
+  const V4<R> vj = load4(b.v + j);
+  const int dcz = (int)((e >> 29) & 3u) - 1;
+  const R cz = (e & 0x80000000u) ? R(dcz) : R(0);
+  const R vx = vi.x - vj.x + cz * K.shear_Lz;
+  const R vy = vi.y - vj.y, vz = vi.z - vj.z;
+  const R r = sqrt(r2);
+  const R ir = R(1) / r;
+  const R w = R(1) - r * K.inv_rc;
+  const R ev = (dx * vx + dy * vy + dz * vz) * ir;
+  const R theta = pair_uniform<R>(g, n1, gi, b.gid[j]);
+  const R f = (-K.dpd_xi * w * ev + K.dpd_amp * theta) * w * ir;
+  tx += f * dx;
+  ty += f * dy;
+  tz += f * dz;
+}
+
+// DPD: the kicked half-step velocities, held back while k_force still read
+// the old ones of the neighbours, become the particles' velocities.
+template <class R>
+__global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                               Bufs<R> s1, Work w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const Bufs<R> &b = d->cur ? s1 : s0;
+  b.v[i] = reinterpret_cast<const V4<R> *>(w.vnew)[i];
+}
+
 // One thread per particle; each warp streams its 32 particles' list rows
 // (column-major: row k holds entry k of all 32 lanes, 128 B) through a
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
-template <class R, bool BONDS>
-__global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force(Geom g, Dyn *__restrict__ d,
+template <class R, bool BONDS, bool DPD>
+__global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? 5 : 3)) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
   __shared__ long long s_red[2][kForceWarps];
@@ -490,8 +538,15 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
 
   const R rc2 = K.rc2, sig2 = K.sig2, eps24 = K.eps24, eps48 = R(2) * K.eps24;
   R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
+  R tdx = R(0), tdy = R(0), tdz = R(0);  // DPD pair forces
   V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
   if (active) pi = b.p[i];
+  V4<R> vi = make4<R>(R(0), R(0), R(0), R(0));
+  int gi = 0;
+  if (DPD && active) {
+    vi = b.v[i];
+    gi = b.gid[i];
+  }
   bool ok = true;
   int waited = 0;  // chunks whose barrier has been passed
   for (int c = 0; c < nchunks; ++c) {
@@ -515,11 +570,18 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
       lj_pair<R>(pi, q1, e1, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
       lj_pair<R>(pi, q2, e2, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
       lj_pair<R>(pi, q3, e3, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      if constexpr (DPD) {
+        dpd_pair<R>(g, pi, vi, gi, b, e0, G, n1, rc2, tdx, tdy, tdz);
+        dpd_pair<R>(g, pi, vi, gi, b, e1, G, n1, rc2, tdx, tdy, tdz);
+        dpd_pair<R>(g, pi, vi, gi, b, e2, G, n1, rc2, tdx, tdy, tdz);
+        dpd_pair<R>(g, pi, vi, gi, b, e3, G, n1, rc2, tdx, tdy, tdz);
+      }
     }
     for (; r < rn; ++r) {
       const uint32_t e = rows[r][lane];
       const V4<R> q = load4(b.p + (e & kIndexMask));
       lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, n1, rc2, tdx, tdy, tdz);
     }
     __syncwarp();
     if (lane == 0 && c + 2 < nchunks) {
@@ -635,8 +697,8 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     const V4<R> v = b.v[i];
     const R zu = pi.z + pi.w;  // unwrapped z (reference + displacement)
     const R vs = K.shear * (zu - K.half_Lz);
-    R ftx = fx, fty = fy, ftz = fz;
-    if (g.thermostat != 0) {
+    R ftx = fx + tdx, fty = fy + tdy, ftz = fz + tdz;
+    if (g.thermostat == 1 || g.thermostat == 2) {
       // 1: friction on the peculiar velocity (Eq. 5); 2: on the absolute
       // velocity (the comparison variant of Sec. 2.2), same noise.  Between
       // builds a particle that crossed the top/bottom face is kept unwrapped,
@@ -662,7 +724,10 @@ __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 4 ? 5 : 3) k_force
     }
     b.fc[i] = make4<R>(fx, fy, fz, R(0));
     b.ft[i] = make4<R>(ftx, fty, ftz, R(0));
-    b.v[i] = nv;
+    // DPD reads the other particles' half-step velocities: the kicked ones go
+    // to a scratch array, copied back once every thread has read
+    if constexpr (DPD) reinterpret_cast<V4<R> *>(w.vnew)[i] = nv;
+    else b.v[i] = nv;
     if (!isfinite(ftx + fty + ftz) || !isfinite(nv.x + nv.y + nv.z))
       atomicOr(&d->err, (int)kErrNonfinite);
     if (sample) {
@@ -1336,15 +1401,26 @@ void launch_force(const SysDev &s, int mode, cudaStream_t st) {
   const int nb = blocks_for(s.g.n, s.force_threads);
   const size_t smem = sizeof(long long) * 3 * (size_t)s.g.nbins;
   const bool bonds = s.g.maxb > 0;
-#define FN(R, A, B)                                                                  \
-  do {                                                                               \
-    if (bonds)                                                                       \
-      k_force<R, true><<<nb, s.force_threads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode);  \
-    else                                                                             \
-      k_force<R, false><<<nb, s.force_threads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode); \
+  const bool dpd = s.g.thermostat == 3;
+#define K3(R, BO, DP, A, B) \
+  k_force<R, BO, DP><<<nb, s.force_threads, smem, st>>>(s.g, s.dyn, A, B, s.w, mode)
+#define FN(R, A, B)                   \
+  do {                                \
+    if (dpd) {                        \
+      if (bonds)                      \
+        K3(R, true, true, A, B);      \
+      else                            \
+        K3(R, false, true, A, B);     \
+      k_vcopy<R><<<blocks_for(s.g.n, 256), 256, 0, st>>>(s.g, s.dyn, A, B, s.w); \
+    } else if (bonds) {               \
+      K3(R, true, false, A, B);       \
+    } else {                          \
+      K3(R, false, false, A, B);      \
+    }                                 \
   } while (0)
   LE_DISPATCH(s, FN);
 #undef FN
+#undef K3
 }
 
 static void rebuild_tail(const SysDev &s, cudaStream_t st) {

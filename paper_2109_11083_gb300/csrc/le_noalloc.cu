@@ -119,6 +119,9 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   c.R02 = p->fene_R0 * p->fene_R0;
   c.fene_k = p->fene_k;
   c.ang_k = 0.0;  // no bonds here
+  c.dpd_xi = 0.0;  // no DPD here
+  c.dpd_amp = 0.0;
+  c.inv_rc = 0.0;
   c.mass = p->mass;
   c.bins_per_Lz = 1.0 / box[2];
   KConst<float> &f = g.cf;
@@ -136,6 +139,9 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   f.R02 = (float)c.R02;
   f.fene_k = (float)c.fene_k;
   f.ang_k = 0.f;
+  f.dpd_xi = 0.f;
+  f.dpd_amp = 0.f;
+  f.inv_rc = 0.f;
   f.mass = (float)c.mass;
   f.bins_per_Lz = (float)c.bins_per_Lz;
   // cell grid of edge >= rc + skin
@@ -205,6 +211,7 @@ size_t carve(SysDev &s, unsigned char *base, int64_t n) {
   w.acc_prof = cv.take<long long>(3);
   w.sum_prof = cv.take<double>(2);
   w.cnt_prof = cv.take<long long>(1);
+  w.vnew = nullptr;
   s.stage = cv.take<double>(6 * (size_t)n);
   s.partials = cv.take<double>(16);
   return cv.used;
