@@ -326,6 +326,15 @@ __global__ void k_fold(Geom g, Dyn *__restrict__ d, Work w) {
 // kernel records kErrTimeout instead of spinning on.
 constexpr int kRowsPerChunk = 16;                  // 16 rows x 128 B = 2 KB per stage
 constexpr int kForceWarps = kForceThreads / 32;
+// neighbour gathers in flight per thread in the pair loop, and the FP32
+// kernel's resident blocks per SM the register budget is sized for
+#ifndef LE_FORCE_UNROLL
+#define LE_FORCE_UNROLL 8
+#endif
+#ifndef LE_FORCE_MINB32
+#define LE_FORCE_MINB32 4
+#endif
+constexpr int kForceUnroll = LE_FORCE_UNROLL;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? 5 : 3)) k_force(Geom g, Dyn *__restrict__ d,
+__global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_FORCE_MINB32 : 3)) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
   __shared__ long long s_red[2][kForceWarps];
@@ -559,22 +568,22 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? 5 :
     const uint32_t(*rows)[32] = s_rows[warp][st];
     const int rn = min(kRowsPerChunk, cnt - c * kRowsPerChunk);
     int r = 0;
-    for (; r + 4 <= rn; r += 4) {
-      const uint32_t e0 = rows[r][lane], e1 = rows[r + 1][lane];
-      const uint32_t e2 = rows[r + 2][lane], e3 = rows[r + 3][lane];
-      const V4<R> q0 = load4(b.p + (e0 & kIndexMask));
-      const V4<R> q1 = load4(b.p + (e1 & kIndexMask));
-      const V4<R> q2 = load4(b.p + (e2 & kIndexMask));
-      const V4<R> q3 = load4(b.p + (e3 & kIndexMask));
-      lj_pair<R>(pi, q0, e0, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
-      lj_pair<R>(pi, q1, e1, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
-      lj_pair<R>(pi, q2, e2, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
-      lj_pair<R>(pi, q3, e3, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+    // all gathers of a group are issued before the first is used; the
+    // pairs are still summed in list order (same result for any group size)
+    for (; r + kForceUnroll <= rn; r += kForceUnroll) {
+      uint32_t e[kForceUnroll];
+      V4<R> q[kForceUnroll];
+#pragma unroll
+      for (int u = 0; u < kForceUnroll; ++u) e[u] = rows[r + u][lane];
+#pragma unroll
+      for (int u = 0; u < kForceUnroll; ++u) q[u] = load4(b.p + (e[u] & kIndexMask));
+#pragma unroll
+      for (int u = 0; u < kForceUnroll; ++u)
+        lj_pair<R>(pi, q[u], e[u], G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
       if constexpr (DPD) {
-        dpd_pair<R>(g, pi, vi, gi, b, e0, G, n1, rc2, tdx, tdy, tdz);
-        dpd_pair<R>(g, pi, vi, gi, b, e1, G, n1, rc2, tdx, tdy, tdz);
-        dpd_pair<R>(g, pi, vi, gi, b, e2, G, n1, rc2, tdx, tdy, tdz);
-        dpd_pair<R>(g, pi, vi, gi, b, e3, G, n1, rc2, tdx, tdy, tdz);
+#pragma unroll
+        for (int u = 0; u < kForceUnroll; ++u)
+          dpd_pair<R>(g, pi, vi, gi, b, e[u], G, n1, rc2, tdx, tdy, tdz);
       }
     }
     for (; r < rn; ++r) {
