@@ -32,8 +32,11 @@
 
 namespace le {
 
+// A list or bond entry packs the neighbour's sorted index (high 24 bits) and
+// its 8-bit slot code (low byte): the slot's bit fields then sit inside a
+// float mantissa, so the pair loop decodes each with one logic operation.
 constexpr int kIndexBits = 24;
-constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int kSlotBits = 8;
 constexpr int kNumSlots = 256;   // 8-bit slot codes (90 of them are used)
 // end marker of a particle's bond entries (slot 255 is never a valid code)
 constexpr uint32_t kNoBond = 0xFFFFFFFFu;
@@ -60,6 +63,12 @@ enum ErrBits : int {
 __host__ __device__ inline int slot_code(int k, int dcy, int dcz, int cross) {
   return (k + 3) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7);
 }
+
+__host__ __device__ inline uint32_t make_entry(int j, int slot) {
+  return ((uint32_t)j << kSlotBits) | (uint32_t)slot;
+}
+__host__ __device__ inline int entry_index(uint32_t e) { return (int)(e >> kSlotBits); }
+__host__ __device__ inline int entry_slot(uint32_t e) { return (int)(e & 0xFFu); }
 
 __host__ __device__ inline void slot_decode(int s, int &k, int &dcy, int &dcz, int &cross) {
   k = (s & 7) - 3;

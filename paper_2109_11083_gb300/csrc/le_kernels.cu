@@ -372,10 +372,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // and the cross-face shift s of this step: a handful of ALU operations.
 template <class R> struct SlotGeo {
   R lx, ly, lz, s;
+  // FP32 decode: the fields sit at bits 0, 3 and 5, so their raw values carry
+  // factors 1, 8 and 32, taken out exactly by these power-of-two scalings
+  R ly8, lz32, s32;
 };
 template <class R>
 __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &ox, R &oy, R &oz) {
-  const int slot = (int)(e >> kIndexBits);
+  const int slot = entry_slot(e);
   const int k = (slot & 7) - 3;
   const int dcy = ((slot >> 3) & 3) - 1;
   const int dcz = ((slot >> 5) & 3) - 1;
@@ -385,19 +388,52 @@ __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &
   oz = R(dcz) * G.lz;
 }
 
-// FP32: a small field v becomes a float as (2^23 + v) - 2^23, built with an
-// integer OR into the bits of 2^23 and one float subtraction (no conversion
-// instruction); the bias of each field folds into the subtracted constant.
+// FP32: a slot field f at bit b becomes the float 2^b f as (2^23 + 2^b f) -
+// 2^23, built with one integer AND-OR into the bits of 2^23 and one float
+// subtraction (no shift, no conversion instruction); the field's bias folds
+// into the subtracted constant and the 2^b into the pre-scaled cell edge.
+struct SlotF {
+  float k, dcy8, dcz32, cz32;  // k, 8 dcy, 32 dcz, 32 cz
+};
+__device__ __forceinline__ SlotF slot_fields(uint32_t e) {
+  SlotF f;
+  f.k = __uint_as_float(0x4B000000u | (e & 0x07u)) - 8388611.0f;       // -3..4
+  f.dcy8 = __uint_as_float(0x4B000000u | (e & 0x18u)) - 8388616.0f;    // 8 x (-1..1)
+  f.dcz32 = __uint_as_float(0x4B000000u | (e & 0x60u)) - 8388640.0f;   // 32 x (-1..1)
+  f.cz32 = (e & 0x80u) ? f.dcz32 : 0.0f;
+  return f;
+}
 template <>
 __device__ __forceinline__ void slot_offset<float>(uint32_t e, const SlotGeo<float> &G, float &ox,
                                                    float &oy, float &oz) {
-  const float k = __uint_as_float(0x4B000000u | ((e >> 24) & 7u)) - 8388611.0f;    // -3..4
-  const float dcy = __uint_as_float(0x4B000000u | ((e >> 27) & 3u)) - 8388609.0f;  // -1..1
-  const float dcz = __uint_as_float(0x4B000000u | ((e >> 29) & 3u)) - 8388609.0f;  // -1..1
-  const float cz = (e & 0x80000000u) ? dcz : 0.0f;
-  ox = __fmaf_rn(cz, G.s, k * G.lx);
-  oy = dcy * G.ly;
-  oz = dcz * G.lz;
+  const SlotF f = slot_fields(e);
+  ox = __fmaf_rn(f.cz32, G.s32, f.k * G.lx);
+  oy = f.dcy8 * G.ly8;
+  oz = f.dcz32 * G.lz32;
+}
+
+// Separation d = p_i - (p_j + image offset of the slot).
+template <class R>
+__device__ __forceinline__ void slot_sep(uint32_t e, const SlotGeo<R> &G, const V4<R> &pi,
+                                         const V4<R> &pj, R &dx, R &dy, R &dz) {
+  R ox, oy, oz;
+  slot_offset<R>(e, G, ox, oy, oz);
+  dx = (pi.x - pj.x) + ox;
+  dy = (pi.y - pj.y) + oy;
+  dz = (pi.z - pj.z) + oz;
+}
+
+// FP32: the cell-offset products are fused into the separation (one rounding
+// fewer per component than adding a rounded offset, three instructions fewer
+// per pair); mirrored slots still give exactly d_ji = -d_ij.
+template <>
+__device__ __forceinline__ void slot_sep<float>(uint32_t e, const SlotGeo<float> &G,
+                                                const V4<float> &pi, const V4<float> &pj,
+                                                float &dx, float &dy, float &dz) {
+  const SlotF f = slot_fields(e);
+  dx = __fmaf_rn(f.cz32, G.s32, __fmaf_rn(f.k, G.lx, pi.x - pj.x));
+  dy = __fmaf_rn(f.dcy8, G.ly8, pi.y - pj.y);
+  dz = __fmaf_rn(f.dcz32, G.lz32, pi.z - pj.z);
 }
 
 // A per-particle sample value in 2^-30 fixed point (the scale is a power of
@@ -418,11 +454,8 @@ template <class R>
 __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
                                         const SlotGeo<R> &G, R rc2, R sig2, R eps24, R eps48,
                                         R &fx, R &fy, R &fz, R &vir) {
-  R ox, oy, oz;
-  slot_offset<R>(e, G, ox, oy, oz);
-  const R dx = (pi.x - pj.x) + ox;
-  const R dy = (pi.y - pj.y) + oy;
-  const R dz = (pi.z - pj.z) + oz;
+  R dx, dy, dz;
+  slot_sep<R>(e, G, pi, pj, dx, dy, dz);
   const R r2 = dx * dx + dy * dy + dz * dz;
   // branch-free: nearly every row has some lane inside rc, so the warp would
   // execute the body anyway; lanes outside get a zero factor
@@ -450,19 +483,16 @@ template <class R>
 __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V4<R> &vi, int gi,
                                          const Bufs<R> &b, uint32_t e, const SlotGeo<R> &G,
                                          long long n1, R rc2, R &tx, R &ty, R &tz) {
-  const int j = (int)(e & kIndexMask);
+  const int j = entry_index(e);
   const V4<R> pj = load4(b.p + j);
-  R ox, oy, oz;
-  slot_offset<R>(e, G, ox, oy, oz);
-  const R dx = (pi.x - pj.x) + ox;
-  const R dy = (pi.y - pj.y) + oy;
-  const R dz = (pi.z - pj.z) + oz;
+  R dx, dy, dz;
+  slot_sep<R>(e, G, pi, pj, dx, dy, dz);
   const R r2 = dx * dx + dy * dy + dz * dz;
   if (!(r2 < rc2)) return;
   const KConst<R> &K = kc<R>(g);
   const V4<R> vj = load4(b.v + j);
-  const int dcz = (int)((e >> 29) & 3u) - 1;
-  const R cz = (e & 0x80000000u) ? R(dcz) : R(0);
+  const int dcz = ((entry_slot(e) >> 5) & 3) - 1;
+  const R cz = (e & 0x80u) ? R(dcz) : R(0);
   const R vx = vi.x - vj.x + cz * K.shear_Lz;
   const R vy = vi.y - vj.y, vz = vi.z - vj.z;
   const R r = sqrt(r2);
@@ -510,11 +540,17 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
     G.ly = g.lc_hi[1];
     G.lz = g.lc_hi[2];
     G.s = d->s_f;
+    G.ly8 = G.ly * 0.125f;
+    G.lz32 = G.lz * 0.03125f;
+    G.s32 = G.s * 0.03125f;
   } else {
     G.lx = g.lc[0];
     G.ly = g.lc[1];
     G.lz = g.lc[2];
     G.s = d->s;
+    G.ly8 = G.ly * 0.125;
+    G.lz32 = G.lz * 0.03125;
+    G.s32 = G.s * 0.03125;
   }
   const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
@@ -570,25 +606,27 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
     int r = 0;
     // all gathers of a group are issued before the first is used; the
     // pairs are still summed in list order (same result for any group size)
-    for (; r + kForceUnroll <= rn; r += kForceUnroll) {
-      uint32_t e[kForceUnroll];
-      V4<R> q[kForceUnroll];
+    // (FP64 and DPD keep four: their larger register state would spill)
+    constexpr int U = (sizeof(R) == 4 && !DPD) ? kForceUnroll : 4;
+    for (; r + U <= rn; r += U) {
+      uint32_t e[U];
+      V4<R> q[U];
 #pragma unroll
-      for (int u = 0; u < kForceUnroll; ++u) e[u] = rows[r + u][lane];
+      for (int u = 0; u < U; ++u) e[u] = rows[r + u][lane];
 #pragma unroll
-      for (int u = 0; u < kForceUnroll; ++u) q[u] = load4(b.p + (e[u] & kIndexMask));
+      for (int u = 0; u < U; ++u) q[u] = load4(b.p + entry_index(e[u]));
 #pragma unroll
-      for (int u = 0; u < kForceUnroll; ++u)
+      for (int u = 0; u < U; ++u)
         lj_pair<R>(pi, q[u], e[u], G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
       if constexpr (DPD) {
 #pragma unroll
-        for (int u = 0; u < kForceUnroll; ++u)
+        for (int u = 0; u < U; ++u)
           dpd_pair<R>(g, pi, vi, gi, b, e[u], G, n1, rc2, tdx, tdy, tdz);
       }
     }
     for (; r < rn; ++r) {
       const uint32_t e = rows[r][lane];
-      const V4<R> q = load4(b.p + (e & kIndexMask));
+      const V4<R> q = load4(b.p + entry_index(e));
       lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
       if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, n1, rc2, tdx, tdy, tdz);
     }
@@ -614,7 +652,7 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
       for (int q = 0; q < g.maxb; ++q) {
         const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
         if (e == kNoBond) break;
-        const int j = (int)(e & kIndexMask);
+        const int j = entry_index(e);
         const V4<R> pj = load4(b.p + j);
         R ox, oy, oz;
         slot_offset<R>(e, G, ox, oy, oz);
@@ -642,7 +680,7 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
         // image arithmetic.
         const R ka = K.ang_k;
         auto sep = [&](const V4<R> &po, uint32_t e, R &ax, R &ay, R &az) {
-          const V4<R> pq = load4(b.p + (e & kIndexMask));
+          const V4<R> pq = load4(b.p + entry_index(e));
           R ox, oy, oz;
           slot_offset<R>(e, G, ox, oy, oz);
           ax = (po.x - pq.x) + ox;
@@ -683,12 +721,12 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
             fz -= az + cz;
           }
           // i at an end: the angles in the middle of j, with j's other bonds
-          const int j = (int)(eu & kIndexMask);
+          const int j = entry_index(eu);
           const V4<R> pj = load4(b.p + j);
           for (int q = 0; q < g.maxb; ++q) {
             const uint32_t ek = w.bond_e[(size_t)j * g.maxb + q];
             if (ek == kNoBond) break;
-            if ((int)(ek & kIndexMask) == i) continue;  // the bond back to i
+            if (entry_index(ek) == i) continue;  // the bond back to i
             R kx, ky, kz;  // r_j - r_k
             sep(pj, ek, kx, ky, kz);
             R ax, ay, az;
@@ -1111,12 +1149,12 @@ __global__ void __launch_bounds__(kListMaxThreads, 4) k_rb_list(Geom g, Dyn *__r
           const int j0 = min(max(w.cell_start[cj], 0), g.n);
           const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
           const bool self_slot = (slot == slot_code(0, 0, 0, 0));
-          const uint32_t tag = (uint32_t)slot << kIndexBits;
+          const uint32_t tag = (uint32_t)slot;
           int j = j0;
           auto emit = [&](int jj, const float4 &q) {
             const float dx = ax - q.x, dy = ay - q.y, dz = az - q.z;
             if (dx * dx + dy * dy + dz * dz < rl2 && !(self_slot && jj == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = (uint32_t)jj | tag;
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = ((uint32_t)jj << kSlotBits) | tag;
               ++cnt;
             }
           };
@@ -1193,7 +1231,7 @@ __global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, B
           (cross && dcz == 0)) {
         atomicOr(&d->err, (int)kErrSlot);
       } else {
-        entry = (uint32_t)j | ((uint32_t)slot_code(kk, dcy, dcz, cross) << kIndexBits);
+        entry = make_entry(j, slot_code(kk, dcy, dcz, cross));
       }
     }
     w.bond_e[(size_t)k * g.maxb + q] = entry;
@@ -1298,13 +1336,13 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
     const uint32_t *nl = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
     for (int k = 0; k < cnt; ++k) {
       const uint32_t e = nl[(size_t)k * 32u];
-      pair((int)(e & kIndexMask), (int)(e >> kIndexBits), false);
+      pair(entry_index(e), entry_slot(e), false);
     }
     if constexpr (BONDS) {
       for (int q = 0; q < g.maxb; ++q) {
         const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
         if (e == kNoBond) break;
-        pair((int)(e & kIndexMask), (int)(e >> kIndexBits), true);
+        pair(entry_index(e), entry_slot(e), true);
       }
       if (g.cd.ang_k != 0.0) {
         // Eq. 12 (k_a (1 + cos theta)): the energy once per angle at its
@@ -1313,12 +1351,12 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
         auto sepd = [&](int o, uint32_t e, double dd[3]) {
           double xo[3], xq[3];
           int co[3], cq[3];
-          const int q = (int)(e & kIndexMask);
+          const int q = entry_index(e);
           absolute_position<R>(g, b, o, xo);
           absolute_position<R>(g, b, q, xq);
           cell_coords(g, __float_as_int(b.pb[o].w), co[0], co[1], co[2]);
           cell_coords(g, __float_as_int(b.pb[q].w), cq[0], cq[1], cq[2]);
-          const int slot = (int)(e >> kIndexBits);
+          const int slot = entry_slot(e);
           for (int a = 0; a < 3; ++a)
             dd[a] = ((xo[a] - ((double)co[a] + 0.5) * g.lc[a]) -
                      (xq[a] - ((double)cq[a] + 0.5) * g.lc[a])) + s_off[slot][a];
@@ -1349,11 +1387,11 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
             }
             acc[9] += ka * (1.0 + cosang(a, c, ah, ch, la));
           }
-          const int j = (int)(eu & kIndexMask);
+          const int j = entry_index(eu);
           for (int q = 0; q < g.maxb; ++q) {
             const uint32_t ek = w.bond_e[(size_t)j * g.maxb + q];
             if (ek == kNoBond) break;
-            if ((int)(ek & kIndexMask) == i) continue;
+            if (entry_index(ek) == i) continue;
             double dk[3], c[3], ah[3], ch[3], la;
             sepd(j, ek, dk);
             for (int k = 0; k < 3; ++k) c[k] = -dk[k];
