@@ -335,6 +335,15 @@ constexpr int kForceWarps = kForceThreads / 32;
 #define LE_FORCE_MINB32 4
 #endif
 constexpr int kForceUnroll = LE_FORCE_UNROLL;
+// candidate loads in flight per thread in the list build, and its resident
+// blocks of the largest shape per SM
+#ifndef LE_LIST_UNROLL
+#define LE_LIST_UNROLL 6
+#endif
+#ifndef LE_LIST_MINB
+#define LE_LIST_MINB 4
+#endif
+constexpr int kListUnroll = LE_LIST_UNROLL;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -452,19 +461,18 @@ template <> __device__ __forceinline__ float recip<float>(float x) {
 
 template <class R>
 __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
-                                        const SlotGeo<R> &G, R rc2, R sig2, R eps24, R eps48,
+                                        const SlotGeo<R> &G, R rc2, R c12, R c6,
                                         R &fx, R &fy, R &fz, R &vir) {
   R dx, dy, dz;
   slot_sep<R>(e, G, pi, pj, dx, dy, dz);
   const R r2 = dx * dx + dy * dy + dz * dz;
   // branch-free: nearly every row has some lane inside rc, so the warp would
-  // execute the body anyway; lanes outside get a zero factor
-  const bool in = r2 < rc2;
-  const R ir2 = recip<R>(in ? r2 : R(1));
-  const R s2 = sig2 * ir2;
-  const R s6 = s2 * s2 * s2;
-  // 24 eps (2 s^12 - s^6) / r^2
-  const R fr = in ? ir2 * s6 * fma(eps48, s6, -eps24) : R(0);
+  // execute the body anyway; lanes outside get a zero factor (r2 > 0 for
+  // every list entry, so the reciprocal is finite either way)
+  const R ir2 = recip<R>(r2);
+  const R ir6 = ir2 * ir2 * ir2;
+  // 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r^2 = ir2 ir6 (c12 ir6 - c6)
+  const R fr = r2 < rc2 ? ir2 * ir6 * fma(c12, ir6, -c6) : R(0);
   const R tx = fr * dx;
   fx += tx;
   fy += fr * dy;
@@ -581,7 +589,10 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
   if (lane == 0)
     for (int c = 0; c < min(2, nchunks); ++c) issue(c);
 
-  const R rc2 = K.rc2, sig2 = K.sig2, eps24 = K.eps24, eps48 = R(2) * K.eps24;
+  const R rc2 = K.rc2;
+  // c6 = 24 eps sigma^6, c12 = 48 eps sigma^12
+  const R sig6 = K.sig2 * K.sig2 * K.sig2;
+  const R c6 = K.eps24 * sig6, c12 = R(2) * c6 * sig6;
   R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
   R tdx = R(0), tdy = R(0), tdz = R(0);  // DPD pair forces
   V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
@@ -617,7 +628,7 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
       for (int u = 0; u < U; ++u) q[u] = load4(b.p + entry_index(e[u]));
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        lj_pair<R>(pi, q[u], e[u], G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+        lj_pair<R>(pi, q[u], e[u], G, rc2, c12, c6, fx, fy, fz, vir);
       if constexpr (DPD) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_
     for (; r < rn; ++r) {
       const uint32_t e = rows[r][lane];
       const V4<R> q = load4(b.p + entry_index(e));
-      lj_pair<R>(pi, q, e, G, rc2, sig2, eps24, eps48, fx, fy, fz, vir);
+      lj_pair<R>(pi, q, e, G, rc2, c12, c6, fx, fy, fz, vir);
       if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, n1, rc2, tdx, tdy, tdz);
     }
     __syncwarp();
@@ -1101,7 +1112,7 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // (f_build/lx decides whether the window reaches a 4th cell).  Rows and
 // cells whose box lies farther than rl from the particle are skipped.
 template <class R>
-__global__ void __launch_bounds__(kListMaxThreads, 4) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                          Bufs<R> s1, Work w, int target_cur) {
   __shared__ float s_offx[kNumSlots];
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
@@ -1158,14 +1169,13 @@ __global__ void __launch_bounds__(kListMaxThreads, 4) k_rb_list(Geom g, Dyn *__r
               ++cnt;
             }
           };
-          // four candidates per pass: their loads are in flight together
-          for (; j + 3 < j1; j += 4) {
-            const float4 qa = __ldg(b.pb + j), qb = __ldg(b.pb + j + 1);
-            const float4 qc = __ldg(b.pb + j + 2), qd = __ldg(b.pb + j + 3);
-            emit(j, qa);
-            emit(j + 1, qb);
-            emit(j + 2, qc);
-            emit(j + 3, qd);
+          // kListUnroll candidates per pass: their loads are in flight together
+          for (; j + kListUnroll <= j1; j += kListUnroll) {
+            float4 q[kListUnroll];
+#pragma unroll
+            for (int u = 0; u < kListUnroll; ++u) q[u] = __ldg(b.pb + j + u);
+#pragma unroll
+            for (int u = 0; u < kListUnroll; ++u) emit(j + u, q[u]);
           }
           for (; j < j1; ++j) emit(j, __ldg(b.pb + j));
         }
