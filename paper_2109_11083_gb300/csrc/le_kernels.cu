@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, DPD ? 2 : (sizeof(R) == 4 ? LE_FORCE_MINB32 : 3)) k_force(Geom g, Dyn *__restrict__ d,
+__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(Geom g, Dyn *__restrict__ d,
                                                          Bufs<R> s0, Bufs<R> s1, Work w,
                                                          int mode) {
   __shared__ long long s_red[2][kForceWarps];
