@@ -240,7 +240,7 @@ def run_ours(args):
     sim.step(args.warmup)
     # launch shapes from the autotuner (trial steps are rolled back: the
     # state and every later result are the same as without it)
-    tuned = None if args.eager else sim.tune(32)
+    tuned = None if args.eager else sim.tune(64)
     c0 = sim.counters()
 
     def barrier():

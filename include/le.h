@@ -205,10 +205,11 @@ LE_API le_status le_get_counters(le_sim *s, le_counters *out);
  * effect at the next step (captured graphs are dropped).
  *
  * le_tune: the autotuner.  Times every pair of force_threads in {128, 256}
- * and list_threads in {64, 128, 256} on this system, over 2 x 16 steps of
- * its own step graph each (list builds included: steps_per_trial >= 16 is
- * rounded to whole 16-step chunks), restoring the state before and after
- * every trial, and keeps the fastest.  The state after le_tune is the state
+ * and list_threads in {64, 128, 256} on this system with its own step graph
+ * (list builds included): one 16-step warm-up chunk, then steps_per_trial
+ * steps (rounded down to whole 16-step chunks, at least one), restoring the
+ * state before and after every trial.  Two sweeps over the shapes; each
+ * shape is scored by its faster trial and the fastest shape is kept.  The state after le_tune is the state
  * before it.  best_force / best_list (nullable) receive the choice;
  * ms_per_step (nullable) its measured time per step. */
 LE_API le_status le_set_launch(le_sim *s, int force_threads, int list_threads);

@@ -910,6 +910,9 @@ LE_API le_status le_tune(le_sim *s, int steps_per_trial, int *best_force, int *b
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   le_status st = LE_OK;
+  // two sweeps over the shapes, each shape scored by its faster trial
+  double tmin[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  for (int rep = 0; rep < 2 && st == LE_OK; ++rep)
   for (int a = 0; a < 2 && st == LE_OK; ++a)
     for (int c = 0; c < 3 && st == LE_OK; ++c) {
       s->s.force_threads = forces[a];
@@ -931,12 +934,15 @@ LE_API le_status le_tune(le_sim *s, int steps_per_trial, int *best_force, int *b
         break;
       }
       const double per = (double)ms / (double)(chunks * kChunk);
-      if (best == 0.0 || per < best) {
-        best = per;
+      if (tmin[a][c] == 0.0 || per < tmin[a][c]) tmin[a][c] = per;
+    }
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < 3; ++c)
+      if (tmin[a][c] > 0.0 && (best == 0.0 || tmin[a][c] < best)) {
+        best = tmin[a][c];
         bf = forces[a];
         bl = lists[c];
       }
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s->s.force_threads = bf;
