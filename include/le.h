@@ -248,11 +248,15 @@ LE_API le_status le_estimate_device_bytes(const double box[3], double shear_rate
 
 /* ---------------------------------------------------------------- batches
  * A batch advances many independent handles (boxes of uneven size, shear
- * rates, parameters) with ONE CUDA-graph launch per 16 steps: every member's
- * step chain (the same kernels as le_step, including the device-decided
- * rebuild branch) is a separate branch of the graph, so members run
- * concurrently on the device.  Each member's trajectory is bit-identical to
- * stepping it alone with le_step.  Members remain ordinary handles (their
+ * rates, parameters) with ONE CUDA-graph launch per 16 steps.  Members that
+ * share precision, bonds and thermostat kind form a group, and each kernel
+ * of a step (drift, decide, the rebuild kernels, pair forces) is ONE launch
+ * for the whole group: each block finds its member in a prefix table of
+ * block counts and runs that member's own kernel code on its own data; the
+ * rebuild kernels run every step, and blocks of members whose trigger did
+ * not fire return at once.  A group launches with its first member's launch
+ * shapes.  Each member's trajectory is bit-identical to stepping it alone
+ * with le_step.  Members remain ordinary handles (their
  * outputs are read with le_forces, le_stress, ...), must have particles,
  * must not be stepped on their own while in a batch, and stay owned by the
  * caller.  The memory budget (0: none) bounds the sum of the members'

@@ -1047,6 +1047,14 @@ LE_API le_status le_set_state(le_sim *s, const void *buf, size_t bytes) {
 // one batch capture, so the graph holds one branch per member and the device
 // runs the members' kernels concurrently.  The kernels are the members' own,
 // so every member's trajectory is bit-identical to stepping it alone.
+// Device tables of one batch group (members sharing precision, bonds,
+// thermostat kind): the member records and the per-kind block prefixes.
+struct BatchGroup {
+  le::BatchGrid grid;
+  void *d_mem = nullptr;
+  int *d_off = nullptr;
+};
+
 struct le_batch {
   size_t budget = 0;
   cudaStream_t stream = nullptr;
@@ -1054,7 +1062,7 @@ struct le_batch {
   cudaStream_t cap = nullptr;
   std::vector<le_sim *> members;
   cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
-  std::vector<cudaEvent_t> events;
+  std::vector<BatchGroup> groups;
   std::string err;
 };
 
@@ -1069,29 +1077,109 @@ void batch_drop_graphs(le_batch *b) {
   if (b->exec_chunk) cudaGraphExecDestroy(b->exec_chunk);
   if (b->exec_one) cudaGraphExecDestroy(b->exec_one);
   b->exec_chunk = b->exec_one = nullptr;
+  // the tables hold member pointers, shapes and capacities: rebuilt with the graphs
+  for (BatchGroup &gr : b->groups) {
+    if (gr.d_mem) cudaFree(gr.d_mem);
+    if (gr.d_off) cudaFree(gr.d_off);
+  }
+  b->groups.clear();
+}
+
+template <class R>
+void fill_members(const std::vector<le_sim *> &sims, std::vector<MemberDev<R>> &out) {
+  out.resize(sims.size());
+  for (size_t k = 0; k < sims.size(); ++k) {
+    const SysDev &sd = sims[k]->s;
+    MemberDev<R> &m = out[k];
+    m.g = sd.g;
+    m.d = sd.dyn;
+    if constexpr (sizeof(R) == 4) {
+      m.s0 = sd.f32[0];
+      m.s1 = sd.f32[1];
+    } else {
+      m.s0 = sd.f64[0];
+      m.s1 = sd.f64[1];
+    }
+    m.w = sd.w;
+    m.sort_part = sd.sort_part;
+    m.sort_passes = sd.sort_passes;
+    m.sort_blocks = sd.sort_blocks;
+  }
+}
+
+// Groups the members and uploads each group's tables.  All members of a
+// group launch with the first member's shapes (shapes change no result).
+le_status batch_build_groups(le_batch *b) {
+  std::map<std::tuple<int, int, int>, std::vector<le_sim *>> bykey;
+  for (le_sim *s : b->members)
+    bykey[std::make_tuple(s->s.prec, s->s.g.maxb > 0 ? 1 : 0,
+                          s->s.g.thermostat == LE_THERMO_DPD ? 1 : 0)]
+        .push_back(s);
+  for (auto &kv : bykey) {
+    const std::vector<le_sim *> &sims = kv.second;
+    BatchGroup gr;
+    BatchGrid &bg = gr.grid;
+    bg.M = (int)sims.size();
+    bg.prec = std::get<0>(kv.first);
+    bg.bonds = std::get<1>(kv.first);
+    bg.dpd = std::get<2>(kv.first);
+    bg.force_threads = sims[0]->s.force_threads;
+    bg.list_threads = sims[0]->s.list_threads;
+    bg.nbins = 1;
+    bg.passes = 1;
+    const int M1 = bg.M + 1;
+    std::vector<int> off((size_t)kBKinds * M1, 0);
+    for (int k = 0; k < bg.M; ++k) {
+      const SysDev &sd = sims[k]->s;
+      bg.nbins = std::max(bg.nbins, sd.g.nbins);
+      bg.passes = std::max(bg.passes, sd.sort_passes);
+      int cnt[kBKinds];
+      cnt[kB256] = blocks_for(sd.g.n, 256);
+      cnt[kBForce] = blocks_for(sd.g.n, bg.force_threads);
+      cnt[kBList] = blocks_for(sd.g.n, bg.list_threads);
+      cnt[kBSort] = sd.sort_blocks;
+      cnt[kBOne] = 1;
+      for (int p = 0; p < kMaxSortPasses; ++p)
+        cnt[kBScan0 + p] = sort_scan_blocks(sd.g.sort_bits, sd.sort_blocks, p);
+      for (int kind = 0; kind < kBKinds; ++kind)
+        off[(size_t)kind * M1 + k + 1] = off[(size_t)kind * M1 + k] + cnt[kind];
+    }
+    for (int kind = 0; kind < kBKinds; ++kind) bg.blocks[kind] = off[(size_t)kind * M1 + bg.M];
+    size_t mem_bytes = 0;
+    std::vector<MemberDev<float>> mf;
+    std::vector<MemberDev<double>> md;
+    const void *host_mem = nullptr;
+    if (bg.prec == 1) {
+      fill_members(sims, mf);
+      host_mem = mf.data();
+      mem_bytes = mf.size() * sizeof(MemberDev<float>);
+    } else {
+      fill_members(sims, md);
+      host_mem = md.data();
+      mem_bytes = md.size() * sizeof(MemberDev<double>);
+    }
+    cudaError_t ce = cudaMalloc(&gr.d_mem, mem_bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&gr.d_off, off.size() * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemcpy(gr.d_mem, host_mem, mem_bytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(gr.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    bg.mem = gr.d_mem;
+    bg.off = gr.d_off;
+    b->groups.push_back(gr);
+    if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(ce));
+  }
+  return LE_OK;
 }
 
 le_status batch_capture(le_batch *b, int steps, cudaGraphExec_t *out) {
-  const size_t m = b->members.size();
-  while (b->events.size() < m + 1) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return bfail(b, LE_ERR_CUDA, "event creation failed");
-    b->events.push_back(e);
+  if (b->groups.empty()) {
+    le_status st = batch_build_groups(b);
+    if (st != LE_OK) return st;
   }
   cudaError_t ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, cudaGetErrorString(ce));
-  cudaGraph_t graph = nullptr;
-  cudaStreamCaptureStatus cs;
-  ce = cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
-  if (ce == cudaSuccess) ce = cudaEventRecord(b->events[m], b->cap);  // fork point
-  for (size_t k = 0; k < m && ce == cudaSuccess; ++k) {
-    le_sim *s = b->members[k];
-    ce = cudaStreamWaitEvent(s->cap_main, b->events[m], 0);
-    if (ce == cudaSuccess) ce = record_steps(s, s->cap_main, graph, steps, nullptr);
-    if (ce == cudaSuccess) ce = cudaEventRecord(b->events[k], s->cap_main);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->events[k], 0);  // join
-  }
+  for (int k = 0; k < steps; ++k)
+    for (const BatchGroup &gr : b->groups) launch_batch_step(gr.grid, b->cap);
   cudaGraph_t captured = nullptr;
   cudaError_t ee = cudaStreamEndCapture(b->cap, &captured);
   if (ce == cudaSuccess) ce = ee;
@@ -1333,7 +1421,6 @@ LE_API le_status le_batch_destroy(le_batch *b) {
   if (!b) return LE_ERR_INVALID_ARG;
   if (b->stream) cudaStreamSynchronize(b->stream);
   batch_drop_graphs(b);
-  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -120,10 +120,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // ------------------------------------------------------------------ k_drift
 template <class R>
-__global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict__ d,
-                                                         Bufs<R> s0, Bufs<R> s1) {
+__device__ __forceinline__ void drift_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bx * blockDim.x + threadIdx.x;
   // time since the build at the step this drift produces
   const float shear_tau = g.cf.shear * (float)(d->step + 1 - d->build_step) * g.cf.dt;
   float disp2 = 0.f;
@@ -169,6 +168,10 @@ __global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict
     if (m > 0.f) atomicMax(&d->maxdisp2, __float_as_uint(m));
   }
 }
+template <class R>
+__global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1) {
+  drift_body<R>(g, d, s0, s1, (int)blockIdx.x);
+}
 
 // x-cell window of the neighbour rows across the top/bottom face for a build
 // with f_b = dX(t_b) mod lx: every cell whose image lies within rl of the
@@ -196,8 +199,7 @@ __device__ __forceinline__ void cross_window(const Geom &g, double fb, Dyn *d) {
 // One block.  Folds the previous step's fixed-point samples into the running
 // sums, advances the step, evaluates the rebuild trigger and fills the slot
 // offset table.
-__global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Work w,
-                                                cudaGraphConditionalHandle h, int use_cond) {
+__device__ __forceinline__ void decide_body(const Geom &g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond, int bx) {
   __shared__ double s_sh;
   __shared__ int need_sh;
   const int t = threadIdx.x;
@@ -292,6 +294,9 @@ __global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Wor
       d->off_build[e][3] = 0.0;
     }
   }
+}
+__global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond) {
+  decide_body(g, d, w, h, use_cond, (int)blockIdx.x);
 }
 
 // Folds pending samples outside the step graph (end of a le_step call).
@@ -487,6 +492,18 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
 // (cz = dcz for a pair across the face, else 0), the time derivative of the
 // slot offset cz s(t).  Each thread evaluates its own side of a pair; the
 // shared theta_ij and the exact antisymmetry of d make F_ji = -F_ij.
+// Rounded operations that the compiler may not contract into FMAs: the DPD
+// pair arithmetic is written with them so that every kernel that inlines it
+// (a system's own step, a batch launch) computes the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class R>
 __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V4<R> &vi, int gi,
                                          const Bufs<R> &b, uint32_t e, const SlotGeo<R> &G,
@@ -495,34 +512,37 @@ __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V
   const V4<R> pj = load4(b.p + j);
   R dx, dy, dz;
   slot_sep<R>(e, G, pi, pj, dx, dy, dz);
-  const R r2 = dx * dx + dy * dy + dz * dz;
+  const R r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
   if (!(r2 < rc2)) return;
   const KConst<R> &K = kc<R>(g);
   const V4<R> vj = load4(b.v + j);
   const int dcz = ((entry_slot(e) >> 5) & 3) - 1;
   const R cz = (e & 0x80u) ? R(dcz) : R(0);
-  const R vx = vi.x - vj.x + cz * K.shear_Lz;
-  const R vy = vi.y - vj.y, vz = vi.z - vj.z;
+  const R vx = add_rn(sub_rn(vi.x, vj.x), mul_rn(cz, K.shear_Lz));
+  const R vy = sub_rn(vi.y, vj.y), vz = sub_rn(vi.z, vj.z);
   const R r = sqrt(r2);
   const R ir = R(1) / r;
-  const R w = R(1) - r * K.inv_rc;
-  const R ev = (dx * vx + dy * vy + dz * vz) * ir;
+  const R w = sub_rn(R(1), mul_rn(r, K.inv_rc));
+  const R ev = mul_rn(fma_rn(dz, vz, fma_rn(dy, vy, mul_rn(dx, vx))), ir);
   const R theta = pair_uniform<R>(g, n1, gi, b.gid[j]);
-  const R f = (-K.dpd_xi * w * ev + K.dpd_amp * theta) * w * ir;
-  tx += f * dx;
-  ty += f * dy;
-  tz += f * dz;
+  const R f = mul_rn(mul_rn(fma_rn(mul_rn(-K.dpd_xi, w), ev, mul_rn(K.dpd_amp, theta)), w), ir);
+  tx = fma_rn(f, dx, tx);
+  ty = fma_rn(f, dy, ty);
+  tz = fma_rn(f, dz, tz);
 }
 
 // DPD: the kicked half-step velocities, held back while k_force still read
 // the old ones of the neighbours, become the particles' velocities.
 template <class R>
-__global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                               Bufs<R> s1, Work w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vcopy_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
+  const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const Bufs<R> &b = d->cur ? s1 : s0;
   b.v[i] = reinterpret_cast<const V4<R> *>(w.vnew)[i];
+}
+template <class R>
+__global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+  vcopy_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
 // One thread per particle; each warp streams its 32 particles' list rows
@@ -530,9 +550,7 @@ __global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(Geom g, Dyn *__restrict__ d,
-                                                         Bufs<R> s0, Bufs<R> s1, Work w,
-                                                         int mode) {
+__device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode, int bx) {
   __shared__ long long s_red[2][kForceWarps];
   __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
   __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
@@ -572,7 +590,7 @@ __global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : L
 
   const Bufs<R> b = pick(cur, s0, s1);
   const KConst<R> &K = kc<R>(g);
-  const int i = blockIdx.x * blockDim.x + t;
+  const int i = bx * blockDim.x + t;
   const bool active = i < g.n;
   const int cnt = active ? min(w.ncount[i], g.maxnb) : 0;
   int kmax = cnt;
@@ -855,7 +873,7 @@ __global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : L
     }
     atomicAdd((unsigned long long *)&d->acc_sxz, (unsigned long long)A);
     atomicAdd((unsigned long long *)&d->acc_ke, (unsigned long long)B);
-    if (blockIdx.x == 0) d->pending = 1;
+    if (bx == 0) d->pending = 1;
   }
   for (int q = t; q < g.nbins; q += blockDim.x) {
     const long long cn = s_prof[g.nbins + q];
@@ -866,6 +884,10 @@ __global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : L
                 (unsigned long long)s_prof[2 * g.nbins + q]);
     }
   }
+}
+template <class R, bool BONDS, bool DPD>
+__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode) {
+  force_body<R, BONDS, DPD>(g, d, s0, s1, w, mode, (int)blockIdx.x);
 }
 
 // --------------------------------------------------------------- rebuild: bin
@@ -912,10 +934,9 @@ __device__ __forceinline__ int wrap_index(int c, int n) {
 // removed, x -= dX as m_b cells + f_b, vx -= shear_rate*Lz), periodic x/y.
 // Writes the new displacement (pre-sort order) and the sort keys/values.
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bin(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                                Bufs<R> s1, Work w) {
+__device__ __forceinline__ void rb_bin_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const float4 q = b.pb[i];
   int c0, c1, c2;
@@ -962,6 +983,10 @@ __global__ void __launch_bounds__(256) k_rb_bin(Geom g, Dyn *__restrict__ d, Buf
   V4<R> *tp = reinterpret_cast<V4<R> *>(w.tmp_p);
   tp[i] = make4<R>(u.h[0], u.h[1], u.h[2], R(0));
   if constexpr (sizeof(R) == 4) w.tmp_lo[i] = make_float4(u.l[0], u.l[1], u.l[2], 0.f);
+}
+template <class R>
+__global__ void __launch_bounds__(256) k_rb_bin(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+  rb_bin_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
 // Initial load: caller-order FP64 positions/velocities (staging) wrapped as
@@ -1014,14 +1039,11 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
 // Gathers the re-based state into cell order.  Forces are not moved: the
 // pair kernel of the same step overwrites them before anything reads them.
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                                    Bufs<R> s1, Work w,
-                                                    const uint32_t *__restrict__ skey,
-                                                    const uint32_t *__restrict__ sval) {
+__device__ __forceinline__ void rb_permute_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval, int bx) {
   const int cur = d->cur;
   const Bufs<R> src = pick(cur, s0, s1);
   const Bufs<R> dst = pick(1 - cur, s0, s1);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int o = min((int)sval[k], g.n - 1);
   const int c = min((int)skey[k], g.ncell - 1);
@@ -1052,18 +1074,24 @@ __global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d,
     w.Xs[3 * (size_t)k + 2] = x2;
   }
 }
+template <class R>
+__global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval) {
+  rb_permute_body<R>(g, d, s0, s1, w, skey, sval, (int)blockIdx.x);
+}
 
 // ----------------------------------------------------------- rebuild: ranges
 // cell_start[c] = first sorted slot of cell c (every entry written once).
-__global__ void __launch_bounds__(256) k_rb_ranges(Geom g, const uint32_t *__restrict__ skey,
-                                                   int *__restrict__ cell_start) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rb_ranges_body(const Geom &g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start, int bx) {
+  const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int c = min((int)skey[k], g.ncell - 1);
   const int prev = k == 0 ? -1 : min((int)skey[k - 1], g.ncell - 1);
   for (int cc = prev + 1; cc <= c; ++cc) cell_start[cc] = k;
   if (k == g.n - 1)
     for (int cc = c + 1; cc <= g.ncell; ++cc) cell_start[cc] = g.n;
+}
+__global__ void __launch_bounds__(256) k_rb_ranges(Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start) {
+  rb_ranges_body(g, skey, cell_start, (int)blockIdx.x);
 }
 
 // Restore path (checkpoint or rollback): sort keys, build-time FP64
@@ -1112,14 +1140,13 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // (f_build/lx decides whether the window reaches a 4th cell).  Rows and
 // cells whose box lies farther than rl from the particle are skipped.
 template <class R>
-__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                                         Bufs<R> s1, Work w, int target_cur) {
+__device__ __forceinline__ void rb_list_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
   __shared__ float s_offx[kNumSlots];
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
   __syncthreads();
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = bx * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < g.n) {
     const float4 qi = b.pb[i];
@@ -1196,16 +1223,19 @@ __global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(Geom 
     atomicAdd((unsigned long long *)&d->list_entries, t);
   }
 }
+template <class R>
+__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+  rb_list_body<R>(g, d, s0, s1, w, target_cur, (int)blockIdx.x);
+}
 
 // ------------------------------------------------------------ rebuild: bonds
 // Slot of every bond: its LE minimum image at the build (FP64), expressed as
 // build-cell offset + image, then matched to the 90-slot table.
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                                  Bufs<R> s1, Work w, int target_cur) {
+__device__ __forceinline__ void rb_bonds_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int gid = b.gid[k];
   const double dXb = d->dX_build;
@@ -1247,8 +1277,15 @@ __global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, B
     w.bond_e[(size_t)k * g.maxb + q] = entry;
   }
 }
+template <class R>
+__global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+  rb_bonds_body<R>(g, d, s0, s1, w, target_cur, (int)blockIdx.x);
+}
 
-__global__ void k_rb_finish(Dyn *__restrict__ d) { d->cur = 1 - d->cur; }
+__device__ __forceinline__ void rb_finish_body(Dyn *__restrict__ d, int bx) { d->cur = 1 - d->cur; }
+__global__ void k_rb_finish(Dyn *__restrict__ d) {
+  rb_finish_body(d, (int)blockIdx.x);
+}
 
 // ------------------------------------------------------------------ exports
 template <class R>
@@ -1429,6 +1466,121 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
   }
 }
 
+
+// ------------------------------------------------------------ batched steps
+// One launch per kernel kind for a whole batch group: each block locates its
+// member in the kind's block prefix table and runs that member's own kernel
+// body; the rebuild kinds exit for members whose step does not rebuild.
+#define LE_MEMBER(KIND)                                            \
+  const int *off_ = off + (KIND) * (M + 1);                        \
+  const int m_ = batch_member(off_, M, (int)blockIdx.x);           \
+  const MemberDev<R> &q = mem[m_];                                 \
+  const int bx_ = (int)blockIdx.x - off_[m_]
+
+template <class R>
+__global__ void __launch_bounds__(kDriftThreads) kb_drift(const MemberDev<R> *__restrict__ mem,
+                                                          const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  drift_body<R>(q.g, q.d, q.s0, q.s1, bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) kb_decide(const MemberDev<R> *__restrict__ mem) {
+  const MemberDev<R> &q = mem[blockIdx.x];
+  decide_body(q.g, q.d, q.w, cudaGraphConditionalHandle(0), 0, 0);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_rb_bin(const MemberDev<R> *__restrict__ mem,
+                                                 const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  if (!q.d->rebuild) return;
+  rb_bin_body<R>(q.g, q.d, q.s0, q.s1, q.w, bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_rb_permute(const MemberDev<R> *__restrict__ mem,
+                                                     const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  if (!q.d->rebuild) return;
+  const int fin = q.sort_passes & 1;
+  rb_permute_body<R>(q.g, q.d, q.s0, q.s1, q.w, q.w.key[fin], q.w.val[fin], bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_rb_ranges(const MemberDev<R> *__restrict__ mem,
+                                                    const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  if (!q.d->rebuild) return;
+  rb_ranges_body(q.g, q.w.key[q.sort_passes & 1], q.w.cell_start, bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kListMaxThreads, 3) kb_rb_list(
+    const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
+  LE_MEMBER(kBList);
+  if (!q.d->rebuild) return;
+  rb_list_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_rb_bonds(const MemberDev<R> *__restrict__ mem,
+                                                   const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  if (!q.d->rebuild || q.g.maxb == 0) return;
+  rb_bonds_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
+}
+
+template <class R>
+__global__ void kb_rb_finish(const MemberDev<R> *__restrict__ mem) {
+  const MemberDev<R> &q = mem[blockIdx.x];
+  if (!q.d->rebuild) return;
+  rb_finish_body(q.d, 0);
+}
+
+template <class R, bool BONDS, bool DPD>
+__global__ void __launch_bounds__(kForceThreads, (DPD && sizeof(R) == 8) ? 1 : (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32)
+    kb_force(const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
+  LE_MEMBER(kBForce);
+  force_body<R, BONDS, DPD>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) kb_vcopy(const MemberDev<R> *__restrict__ mem,
+                                                const int *__restrict__ off, int M) {
+  LE_MEMBER(kB256);
+  vcopy_body<R>(q.g, q.d, q.s0, q.s1, q.w, bx_);
+}
+#undef LE_MEMBER
+
+template <class R>
+void batch_step(const BatchGrid &bg, cudaStream_t st) {
+  const MemberDev<R> *mem = static_cast<const MemberDev<R> *>(bg.mem);
+  const int M = bg.M;
+  const int *off = bg.off;
+  const int n256 = bg.blocks[kB256];
+  kb_drift<R><<<n256, kDriftThreads, 0, st>>>(mem, off, M);
+  kb_decide<R><<<M, 128, 0, st>>>(mem);
+  kb_rb_bin<R><<<n256, 256, 0, st>>>(mem, off, M);
+  launch_batch_sort(bg, st);
+  kb_rb_permute<R><<<n256, 256, 0, st>>>(mem, off, M);
+  kb_rb_ranges<R><<<n256, 256, 0, st>>>(mem, off, M);
+  kb_rb_list<R><<<bg.blocks[kBList], bg.list_threads, 0, st>>>(mem, off, M);
+  if (bg.bonds) kb_rb_bonds<R><<<n256, 256, 0, st>>>(mem, off, M);
+  kb_rb_finish<R><<<M, 1, 0, st>>>(mem);
+  const size_t smem = sizeof(long long) * 3 * (size_t)bg.nbins;
+  const int nf = bg.blocks[kBForce];
+  if (bg.dpd) {
+    if (bg.bonds) kb_force<R, true, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+    else kb_force<R, false, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+    kb_vcopy<R><<<n256, 256, 0, st>>>(mem, off, M);
+  } else if (bg.bonds) {
+    kb_force<R, true, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+  } else {
+    kb_force<R, false, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -1569,6 +1721,11 @@ void launch_observe(const SysDev &s, cudaStream_t st) {
   } while (0)
   LE_DISPATCH(s, FN);
 #undef FN
+}
+
+void launch_batch_step(const BatchGrid &bg, cudaStream_t st) {
+  if (bg.prec == 1) batch_step<float>(bg, st);
+  else batch_step<double>(bg, st);
 }
 
 }  // namespace le

@@ -60,5 +60,61 @@ int sort_passes_for(int bits);
 size_t sort_scan_parts(int blocks);
 void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,
                       int bits, int blocks, cudaStream_t st);
+// Digit of radix pass p for keys of `bits` bits sorted in `passes` passes.
+__host__ __device__ inline void sort_pass_digit(int bits, int passes, int p, int &shift, int &width) {
+  const int wmax = (bits + passes - 1) / passes;
+  shift = p * wmax;
+  width = bits - shift < wmax ? bits - shift : wmax;
+}
+// Blocks of the count-table scan of pass p (0 when the sort has no pass p).
+int sort_scan_blocks(int bits, int blocks, int p);
+
+// ------------------------------------------------------------ batched steps
+// A batch of independent systems advances with ONE launch per kernel kind:
+// every block finds its system in a per-kind prefix table of block counts
+// and runs that system's own kernel body on its own data, so each member's
+// trajectory is bit-identical to stepping it alone.  The rebuild kernels run
+// every step for every member; blocks of a member whose step decided "no
+// rebuild" exit at once.  Members of one launch share precision, bonds,
+// thermostat kind and launch shapes (a group).
+constexpr int kMaxSortPasses = 4;
+enum BatchKind : int {
+  kB256 = 0,   // blocks_for(n, 256): drift, bin, permute, ranges, bonds, vcopy
+  kBForce,     // blocks_for(n, force_threads)
+  kBList,      // blocks_for(n, list_threads)
+  kBSort,      // sort tiles
+  kBOne,       // one block per member: decide, scan top, finish
+  kBScan0,     // count-table scan blocks of pass p: kBScan0 + p
+  kBKinds = kBScan0 + kMaxSortPasses
+};
+template <class R> struct MemberDev {
+  Geom g;
+  Dyn *d;
+  Bufs<R> s0, s1;
+  Work w;
+  uint32_t *sort_part;
+  int sort_passes, sort_blocks;
+};
+struct BatchGrid {
+  const void *mem = nullptr;  // MemberDev<R>[M] in device memory
+  const int *off = nullptr;   // [kBKinds][M + 1] block prefix per kind, device memory
+  int M = 0;
+  int blocks[kBKinds] = {};   // grid size per kind
+  int prec = 1, bonds = 0, dpd = 0;
+  int force_threads = 256, list_threads = 128, nbins = 1, passes = 1;
+};
+// One step of every member of the group (drift, decide, gated rebuild, force).
+void launch_batch_step(const BatchGrid &bg, cudaStream_t st);
+void launch_batch_sort(const BatchGrid &bg, cudaStream_t st);  // gated radix sort, all passes
+
+__device__ __forceinline__ int batch_member(const int *off, int M, int bid) {
+  int lo = 0, hi = M - 1;  // the last member whose first block is <= bid
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 }  // namespace le

@@ -20,22 +20,23 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
-__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__restrict__ key, int n,
-                                                          int shift, int bits, int nblocks,
-                                                          uint32_t *__restrict__ hist) {
+__device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, int n, int shift, int bits, int nblocks, uint32_t *__restrict__ hist, int bx) {
   __shared__ uint32_t cnt[kSortBuckets];
   const int nb = 1 << bits;
   const uint32_t mask = (uint32_t)nb - 1u;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
-  const int base = blockIdx.x * kSortTile;
+  const int base = bx * kSortTile;
 #pragma unroll 4
   for (int k = 0; k < kSortItems; ++k) {
     const int i = base + k * kSortThreads + threadIdx.x;
     if (i < n) atomicAdd(&cnt[(key[i] >> shift) & mask], 1u);
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(size_t)b * nblocks + blockIdx.x] = cnt[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(size_t)b * nblocks + bx] = cnt[b];
+}
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__restrict__ key, int n, int shift, int bits, int nblocks, uint32_t *__restrict__ hist) {
+  rs_hist_body(key, n, shift, bits, nblocks, hist, (int)blockIdx.x);
 }
 
 // Block-wide inclusive scan of one value per thread (1024 threads).
@@ -62,20 +63,22 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_t
 }
 
 // Pass 1 of the scan: the sum of each chunk of kScanChunk counts.
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t *__restrict__ a, int m,
-                                                            uint32_t *__restrict__ part) {
+__device__ __forceinline__ void scan_sums_body(const uint32_t *__restrict__ a, int m, uint32_t *__restrict__ part, int bx) {
   __shared__ uint32_t wt[32];
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  const int base = bx * kScanChunk + threadIdx.x * kScanItems;
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k)
     if (base + k < m) s += a[base + k];
   const uint32_t incl = block_incl_scan(s, wt);
-  if (threadIdx.x == kScanThreads - 1) part[blockIdx.x] = incl;
+  if (threadIdx.x == kScanThreads - 1) part[bx] = incl;
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t *__restrict__ a, int m, uint32_t *__restrict__ part) {
+  scan_sums_body(a, m, part, (int)blockIdx.x);
 }
 
 // Pass 2: exclusive scan of the chunk sums (one block, up to 4 per thread).
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict__ part, int np) {
+__device__ __forceinline__ void scan_top_body(uint32_t *__restrict__ part, int np, int bx) {
   __shared__ uint32_t wt[32];
   const int base = threadIdx.x * 4;
   uint32_t v[4], s = 0;
@@ -91,30 +94,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict_
     run += v[k];
   }
 }
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict__ part, int np) {
+  scan_top_body(part, np, (int)blockIdx.x);
+}
 
 // Pass 3: exclusive scan inside each chunk, offset by the chunk's start.
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t *__restrict__ a, int m,
-                                                             const uint32_t *__restrict__ part) {
+__device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part, int bx) {
   __shared__ uint32_t wt[32];
-  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  const int base = bx * kScanChunk + threadIdx.x * kScanItems;
   uint32_t v[kScanItems], s = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     v[k] = base + k < m ? a[base + k] : 0u;
     s += v[k];
   }
-  uint32_t run = block_incl_scan(s, wt) - s + part[blockIdx.x];
+  uint32_t run = block_incl_scan(s, wt) - s + part[bx];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     if (base + k < m) a[base + k] = run;
     run += v[k];
   }
 }
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part) {
+  scan_apply_body(a, m, part, (int)blockIdx.x);
+}
 
-__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
-    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks,
-    const uint32_t *__restrict__ hist) {
+__device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks, const uint32_t *__restrict__ hist, int bx) {
   __shared__ uint32_t base[kSortBuckets];          // global start of each digit for this tile
   __shared__ uint32_t wcnt[kWarps][kSortBuckets];  // per-warp counts -> per-warp offsets
   __shared__ uint32_t total[kSortBuckets];
@@ -122,11 +127,11 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
   const uint32_t mask = (uint32_t)nb - 1u;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int b = t; b < nb; b += blockDim.x) {
-    base[b] = hist[(size_t)b * nblocks + blockIdx.x];
+    base[b] = hist[(size_t)b * nblocks + bx];
     for (int w = 0; w < kWarps; ++w) wcnt[w][b] = 0;
   }
   __syncthreads();
-  const int tile = blockIdx.x * kSortTile;
+  const int tile = bx * kSortTile;
   for (int c = 0; c < kSortItems; ++c) {
     const int i = tile + c * kSortThreads + t;
     const bool valid = i < n;
@@ -164,6 +169,86 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
     __syncthreads();
   }
 }
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks, const uint32_t *__restrict__ hist) {
+  rs_scatter_body(kin, vin, kout, vout, n, shift, bits, nblocks, hist, (int)blockIdx.x);
+}
+
+
+// ------------------------------------------------------------ batched sort
+// The same pass kernels for every member of a batch group in one launch;
+// blocks of members that do not rebuild this step (or have no pass p) exit.
+template <class R>
+__global__ void __launch_bounds__(kSortThreads) kb_rs_hist(const MemberDev<R> *__restrict__ mem,
+                                                           const int *__restrict__ off, int M, int p) {
+  const int m = batch_member(off, M, blockIdx.x);
+  const MemberDev<R> &q = mem[m];
+  if (!q.d->rebuild || p >= q.sort_passes) return;
+  int shift, w;
+  sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
+  rs_hist_body(q.w.key[p & 1], q.g.n, shift, w, q.sort_blocks, q.w.hist, (int)blockIdx.x - off[m]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kScanThreads) kb_scan_sums(const MemberDev<R> *__restrict__ mem,
+                                                             const int *__restrict__ off, int M, int p) {
+  const int m = batch_member(off, M, blockIdx.x);
+  const MemberDev<R> &q = mem[m];
+  if (!q.d->rebuild) return;
+  int shift, w;
+  sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
+  scan_sums_body(q.w.hist, (1 << w) * q.sort_blocks, q.sort_part, (int)blockIdx.x - off[m]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *__restrict__ mem, int p) {
+  const MemberDev<R> &q = mem[blockIdx.x];
+  if (!q.d->rebuild || p >= q.sort_passes) return;
+  int shift, w;
+  sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
+  const int mm = (1 << w) * q.sort_blocks;
+  scan_top_body(q.sort_part, (mm + kScanChunk - 1) / kScanChunk, 0);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const MemberDev<R> *__restrict__ mem,
+                                                              const int *__restrict__ off, int M, int p) {
+  const int m = batch_member(off, M, blockIdx.x);
+  const MemberDev<R> &q = mem[m];
+  if (!q.d->rebuild) return;
+  int shift, w;
+  sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
+  scan_apply_body(q.w.hist, (1 << w) * q.sort_blocks, q.sort_part, (int)blockIdx.x - off[m]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kSortThreads) kb_rs_scatter(const MemberDev<R> *__restrict__ mem,
+                                                              const int *__restrict__ off, int M, int p) {
+  const int m = batch_member(off, M, blockIdx.x);
+  const MemberDev<R> &q = mem[m];
+  if (!q.d->rebuild || p >= q.sort_passes) return;
+  int shift, w;
+  sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
+  const int in = p & 1, out = in ^ 1;
+  rs_scatter_body(q.w.key[in], q.w.val[in], q.w.key[out], q.w.val[out], q.g.n, shift, w,
+                  q.sort_blocks, q.w.hist, (int)blockIdx.x - off[m]);
+}
+
+template <class R>
+void batch_sort_passes(const BatchGrid &bg, cudaStream_t st) {
+  const MemberDev<R> *mem = static_cast<const MemberDev<R> *>(bg.mem);
+  const int M = bg.M, M1 = bg.M + 1;
+  const int *off_sort = bg.off + kBSort * M1;
+  for (int p = 0; p < bg.passes; ++p) {
+    const int *off_scan = bg.off + (kBScan0 + p) * M1;
+    const int nscan = bg.blocks[kBScan0 + p];
+    if (nscan == 0) continue;
+    kb_rs_hist<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, off_sort, M, p);
+    kb_scan_sums<R><<<nscan, kScanThreads, 0, st>>>(mem, off_scan, M, p);
+    kb_scan_top<R><<<M, kScanThreads, 0, st>>>(mem, p);
+    kb_scan_apply<R><<<nscan, kScanThreads, 0, st>>>(mem, off_scan, M, p);
+    kb_rs_scatter<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, off_sort, M, p);
+  }
+}
 
 }  // namespace
 
@@ -173,13 +258,21 @@ size_t sort_scan_parts(int blocks) {
   return ((size_t)kSortBuckets * blocks + kScanChunk - 1) / kScanChunk;
 }
 
+int sort_scan_blocks(int bits, int blocks, int p) {
+  const int passes = sort_passes_for(bits);
+  if (p >= passes) return 0;
+  int shift, w;
+  sort_pass_digit(bits, passes, p, shift, w);
+  const int m = (1 << w) * blocks;
+  return (m + kScanChunk - 1) / kScanChunk;
+}
+
 void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,
                       int bits, int blocks, cudaStream_t st) {
   const int passes = sort_passes_for(bits);
-  const int width = (bits + passes - 1) / passes;
   for (int p = 0; p < passes; ++p) {
-    const int shift = p * width;
-    const int w = bits - shift < width ? bits - shift : width;
+    int shift, w;
+    sort_pass_digit(bits, passes, p, shift, w);
     const int in = p & 1, out = in ^ 1;
     const int m = (1 << w) * blocks;
     const int np = (m + kScanChunk - 1) / kScanChunk;
@@ -190,6 +283,11 @@ void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32
     k_rs_scatter<<<blocks, kSortThreads, 0, st>>>(key[in], val[in], key[out], val[out], n, shift,
                                                   w, blocks, hist);
   }
+}
+
+void launch_batch_sort(const BatchGrid &bg, cudaStream_t st) {
+  if (bg.prec == 1) batch_sort_passes<float>(bg, st);
+  else batch_sort_passes<double>(bg, st);
 }
 
 }  // namespace le

@@ -64,3 +64,51 @@ def test_batch_budget_refuses_a_member_beyond_it():
         assert e.value.status == 3
     for s in sims:
         s.close()
+
+
+def _kg(seed, prec):
+    pos, box, bonds = synth.lattice_chains(20, 20, 0.85, seed)
+    vel = synth.mb_velocities(pos.shape[0], 1.0, seed)
+    vel[:, 0] += 0.2 * (pos[:, 2] - 0.5 * box)
+    sim = le.Sim(box, 0.2, 2 ** (1 / 6), 0.3, dt=0.005, xi=0.5, seed=seed, system_id=seed,
+                 precision=prec, angle_k=1.5, profile_bins=8)
+    sim.set_bonds(bonds)
+    sim.set_particles(pos, vel)
+    return sim
+
+
+def _dpd(seed, prec):
+    pos, box = synth.lj_box(1500, 0.8442, seed)
+    vel = synth.mb_velocities(1500, 1.0, seed)
+    vel[:, 0] += 0.4 * (pos[:, 2] - 0.5 * box)
+    sim = le.Sim(box, 0.4, 2.5, 0.3, seed=seed, system_id=seed, precision=prec, xi=4.5,
+                 thermostat=le.LE_THERMO_DPD, profile_bins=8)
+    sim.set_particles(pos, vel)
+    return sim
+
+
+def test_mixed_groups_equal_alone_bitwise():
+    """Members of different precision, with and without bonds, Langevin and
+    DPD, in one batch (several launch groups): each equals its run alone."""
+    specs = synth.batched_systems(count=3, nmin=800, nmax=4000, seed=81)
+
+    def make():
+        return ([_box(s, p) for s, p in zip(specs, (1, 0, 1))] +
+                [_kg(31, 1), _kg(32, 0), _dpd(33, 1), _dpd(34, 0)])
+
+    alone, mixed = make(), make()
+    for a in alone:
+        a.step(48)
+    with le.Batch() as b:
+        for m in mixed:
+            b.add(m)
+        b.step(48)
+    for a, m in zip(alone, mixed):
+        ra, va = a.positions()
+        rm, vm = m.positions()
+        assert np.array_equal(ra, rm) and np.array_equal(va, vm)
+        assert np.array_equal(a.forces(), m.forces())
+        assert a.stress(instantaneous=False)[1] == m.stress(instantaneous=False)[1]
+        assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 0
+    for s in alone + mixed:
+        s.close()
