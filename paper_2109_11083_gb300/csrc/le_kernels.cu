@@ -118,9 +118,19 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Block index of a kernel body: the hardware register for a system's own
+// launch, a stored value for a batched launch (member-relative index).
+struct HwBlock {
+  __device__ __forceinline__ int operator()() const { return (int)blockIdx.x; }
+};
+struct VBlock {
+  int b;
+  __device__ __forceinline__ int operator()() const { return b; }
+};
+
 // ------------------------------------------------------------------ k_drift
 template <class R>
-__device__ __forceinline__ void drift_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, int bx) {
+__device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = bx * blockDim.x + threadIdx.x;
   // time since the build at the step this drift produces
@@ -169,7 +179,7 @@ __device__ __forceinline__ void drift_body(const Geom &g, Dyn *__restrict__ d, B
   }
 }
 template <class R>
-__global__ void __launch_bounds__(kDriftThreads) k_drift(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1) {
+__global__ void __launch_bounds__(kDriftThreads) k_drift(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1) {
   drift_body<R>(g, d, s0, s1, (int)blockIdx.x);
 }
 
@@ -199,7 +209,7 @@ __device__ __forceinline__ void cross_window(const Geom &g, double fb, Dyn *d) {
 // One block.  Folds the previous step's fixed-point samples into the running
 // sums, advances the step, evaluates the rebuild trigger and fills the slot
 // offset table.
-__device__ __forceinline__ void decide_body(const Geom &g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond, int bx) {
+__device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond, int bx) {
   __shared__ double s_sh;
   __shared__ int need_sh;
   const int t = threadIdx.x;
@@ -295,7 +305,7 @@ __device__ __forceinline__ void decide_body(const Geom &g, Dyn *__restrict__ d, 
     }
   }
 }
-__global__ void __launch_bounds__(128) k_decide(Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(128) k_decide(const __grid_constant__ Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond) {
   decide_body(g, d, w, h, use_cond, (int)blockIdx.x);
 }
 
@@ -534,14 +544,14 @@ __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V
 // DPD: the kicked half-step velocities, held back while k_force still read
 // the old ones of the neighbours, become the particles' velocities.
 template <class R>
-__device__ __forceinline__ void vcopy_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
+__device__ __forceinline__ void vcopy_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
   const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const Bufs<R> &b = d->cur ? s1 : s0;
   b.v[i] = reinterpret_cast<const V4<R> *>(w.vnew)[i];
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+__global__ void __launch_bounds__(256) k_vcopy(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
   vcopy_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
@@ -549,8 +559,8 @@ __global__ void __launch_bounds__(256) k_vcopy(Geom g, Dyn *__restrict__ d, Bufs
 // (column-major: row k holds entry k of all 32 lanes, 128 B) through a
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
-template <class R, bool BONDS, bool DPD>
-__device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode, int bx) {
+template <class R, bool BONDS, bool DPD, class BX>
+__device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode, BX bx) {
   __shared__ long long s_red[2][kForceWarps];
   __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
   __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
@@ -590,7 +600,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
 
   const Bufs<R> b = pick(cur, s0, s1);
   const KConst<R> &K = kc<R>(g);
-  const int i = bx * blockDim.x + t;
+  const int i = bx() * blockDim.x + t;
   const bool active = i < g.n;
   const int cnt = active ? min(w.ncount[i], g.maxnb) : 0;
   int kmax = cnt;
@@ -873,7 +883,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
     }
     atomicAdd((unsigned long long *)&d->acc_sxz, (unsigned long long)A);
     atomicAdd((unsigned long long *)&d->acc_ke, (unsigned long long)B);
-    if (bx == 0) d->pending = 1;
+    if (bx() == 0) d->pending = 1;
   }
   for (int q = t; q < g.nbins; q += blockDim.x) {
     const long long cn = s_prof[g.nbins + q];
@@ -886,8 +896,8 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   }
 }
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode) {
-  force_body<R, BONDS, DPD>(g, d, s0, s1, w, mode, (int)blockIdx.x);
+__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode) {
+  force_body<R, BONDS, DPD>(g, d, s0, s1, w, mode, HwBlock{});
 }
 
 // --------------------------------------------------------------- rebuild: bin
@@ -934,7 +944,7 @@ __device__ __forceinline__ int wrap_index(int c, int n) {
 // removed, x -= dX as m_b cells + f_b, vx -= shear_rate*Lz), periodic x/y.
 // Writes the new displacement (pre-sort order) and the sort keys/values.
 template <class R>
-__device__ __forceinline__ void rb_bin_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
+__device__ __forceinline__ void rb_bin_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
@@ -985,7 +995,7 @@ __device__ __forceinline__ void rb_bin_body(const Geom &g, Dyn *__restrict__ d, 
   if constexpr (sizeof(R) == 4) w.tmp_lo[i] = make_float4(u.l[0], u.l[1], u.l[2], 0.f);
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bin(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+__global__ void __launch_bounds__(256) k_rb_bin(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
   rb_bin_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
@@ -1039,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
 // Gathers the re-based state into cell order.  Forces are not moved: the
 // pair kernel of the same step overwrites them before anything reads them.
 template <class R>
-__device__ __forceinline__ void rb_permute_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval, int bx) {
+__device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval, int bx) {
   const int cur = d->cur;
   const Bufs<R> src = pick(cur, s0, s1);
   const Bufs<R> dst = pick(1 - cur, s0, s1);
@@ -1075,13 +1085,13 @@ __device__ __forceinline__ void rb_permute_body(const Geom &g, Dyn *__restrict__
   }
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_permute(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval) {
+__global__ void __launch_bounds__(256) k_rb_permute(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval) {
   rb_permute_body<R>(g, d, s0, s1, w, skey, sval, (int)blockIdx.x);
 }
 
 // ----------------------------------------------------------- rebuild: ranges
 // cell_start[c] = first sorted slot of cell c (every entry written once).
-__device__ __forceinline__ void rb_ranges_body(const Geom &g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start, int bx) {
+__device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start, int bx) {
   const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int c = min((int)skey[k], g.ncell - 1);
@@ -1090,7 +1100,7 @@ __device__ __forceinline__ void rb_ranges_body(const Geom &g, const uint32_t *__
   if (k == g.n - 1)
     for (int cc = c + 1; cc <= g.ncell; ++cc) cell_start[cc] = g.n;
 }
-__global__ void __launch_bounds__(256) k_rb_ranges(Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start) {
+__global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start) {
   rb_ranges_body(g, skey, cell_start, (int)blockIdx.x);
 }
 
@@ -1139,14 +1149,14 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // offset: 3 or 4 cells covering every cell within rl of the shifted row
 // (f_build/lx decides whether the window reaches a 4th cell).  Rows and
 // cells whose box lies farther than rl from the particle are skipped.
-template <class R>
-__device__ __forceinline__ void rb_list_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
+template <class R, class BX>
+__device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, BX bx) {
   __shared__ float s_offx[kNumSlots];
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
   __syncthreads();
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
-  const int i = bx * blockDim.x + threadIdx.x;
+  const int i = bx() * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < g.n) {
     const float4 qi = b.pb[i];
@@ -1224,15 +1234,15 @@ __device__ __forceinline__ void rb_list_body(const Geom &g, Dyn *__restrict__ d,
   }
 }
 template <class R>
-__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
-  rb_list_body<R>(g, d, s0, s1, w, target_cur, (int)blockIdx.x);
+__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+  rb_list_body<R>(g, d, s0, s1, w, target_cur, HwBlock{});
 }
 
 // ------------------------------------------------------------ rebuild: bonds
 // Slot of every bond: its LE minimum image at the build (FP64), expressed as
 // build-cell offset + image, then matched to the 90-slot table.
 template <class R>
-__device__ __forceinline__ void rb_bonds_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
+__device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int k = bx * blockDim.x + threadIdx.x;
@@ -1278,7 +1288,7 @@ __device__ __forceinline__ void rb_bonds_body(const Geom &g, Dyn *__restrict__ d
   }
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bonds(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+__global__ void __launch_bounds__(256) k_rb_bonds(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
   rb_bonds_body<R>(g, d, s0, s1, w, target_cur, (int)blockIdx.x);
 }
 
@@ -1520,7 +1530,7 @@ __global__ void __launch_bounds__(kListMaxThreads, 3) kb_rb_list(
     const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
   LE_MEMBER(kBList);
   if (!q.d->rebuild) return;
-  rb_list_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
+  rb_list_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, VBlock{bx_});
 }
 
 template <class R>
@@ -1539,10 +1549,10 @@ __global__ void kb_rb_finish(const MemberDev<R> *__restrict__ mem) {
 }
 
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, (DPD && sizeof(R) == 8) ? 1 : (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32)
+__global__ void __launch_bounds__(kForceThreads, sizeof(R) == 8 ? 1 : DPD ? 2 : LE_FORCE_MINB32)
     kb_force(const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
   LE_MEMBER(kBForce);
-  force_body<R, BONDS, DPD>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
+  force_body<R, BONDS, DPD>(q.g, q.d, q.s0, q.s1, q.w, 0, VBlock{bx_});
 }
 
 template <class R>
