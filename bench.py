@@ -64,6 +64,36 @@ def dist_info():
     return rank, world, local
 
 
+def shard_systems(specs, rank: int, world: int):
+    """The systems of `rank` among `world` ranks: independent boxes need no
+    exchange, so each goes to exactly one rank, largest first to the least
+    loaded rank (deterministic: every rank computes the same assignment)."""
+    order = sorted(range(len(specs)), key=lambda k: (-specs[k]["n"], k))
+    load = [0] * world
+    owner = [0] * len(specs)
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[k] = r
+        load[r] += specs[k]["n"]
+    return [specs[k] for k in range(len(specs)) if owner[k] == rank]
+
+
+def job_totals(seconds: float, units: float):
+    """Whole-job figures over all ranks: the slowest rank's time and the sum
+    of the units the ranks processed (the rank's own values without a
+    process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(seconds), float(units)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def workload_config(w):
     return {"workload": w.name, "n_particles": w.n, "density": w.rho, "box": round(w.box, 6),
             "rc": w.rc, "skin": w.skin, "shear_rate": w.shear_rate, "dt": w.dt,
@@ -257,11 +287,9 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     c1 = sim.counters()
-    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = w.n * world * args.steps / (max_ms * 1e-3)
+    max_s, units = job_totals(total_ms * 1e-3, w.n * args.steps)
+    max_ms = max_s * 1e3
+    value = units / max_s
 
     rebuilds = c1["rebuilds"] - c0["rebuilds"]
     ncell = c1["cells"][0] * c1["cells"][1] * c1["cells"][2]
@@ -351,9 +379,24 @@ def run_batched(args):
     """Config 4: independent LJ boxes of uneven N stepped one handle at a time
     (plain) and all together in one batch, equal accuracy checked bitwise."""
     import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
     import paper_2109_11083_gb300 as le
-    specs = synth.batched_systems(count=args.systems)
+    all_specs = synth.batched_systems(count=args.systems)
+    # N > 1: the boxes are sharded over the ranks (no exchange); the total work
+    # is fixed, so this is strong scaling
+    specs = shard_systems(all_specs, rank, world) if world > 1 else all_specs
     total = sum(s["n"] for s in specs)
+    total_all = sum(s["n"] for s in all_specs)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
     plain = [make_box_sim(le, s) for s in specs]
     batched = [make_box_sim(le, s) for s in specs]
     tuned = [make_box_sim(le, s) for s in specs]
@@ -376,47 +419,60 @@ def run_batched(args):
     tf, tl, tms = bt.tune(32)
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t0
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for s in plain:
         s.step(args.steps)
-    torch.cuda.synchronize()
+    barrier()
     t_plain = time.perf_counter() - t0
     t0 = time.perf_counter()
     b.step(args.steps)
-    torch.cuda.synchronize()
+    barrier()
     t_untuned = time.perf_counter() - t0
     t0 = time.perf_counter()
     bt.step(args.steps)
-    torch.cuda.synchronize()
+    barrier()
     t_batch = time.perf_counter() - t0
+    t_plain, u_plain = job_totals(t_plain, total * args.steps)
+    t_untuned, u_untuned = job_totals(t_untuned, total * args.steps)
+    t_batch, u_batch = job_totals(t_batch, total * args.steps)
     equal = True
     for k in range(0, len(specs), max(1, len(specs) // 16)):
         rp, vp = plain[k].positions()
         for other in (batched[k], tuned[k]):
             rb, vb = other.positions()
             equal = equal and bool(np.array_equal(rp, rb) and np.array_equal(vp, vb))
-    value = total * args.steps / t_batch
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    if world > 1:  # every rank's members must be equal
+        flag = torch.tensor([1 if equal else 0], device="cuda", dtype=torch.int32)
+        torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MIN)
+        equal = bool(flag.item())
+    value = u_batch / t_batch
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": w, "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched_{len(specs)}_uneven_lj_fp32", "systems": len(specs),
-                       "total_particles": total, "n_range": [500, 32000],
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched_{len(all_specs)}_uneven_lj_fp32",
+                       "systems": len(all_specs), "total_particles": total_all,
+                       "parallelism": f"systems sharded over {world} ranks" if world > 1 else "single",
+                       "n_range": [500, 32000],
                        "density_range": [0.7, 0.9], "shear_range": [1e-3, 1.0], "rc": 2.5,
                        "skin": 0.3, "dt": 0.005},
-            "plain": {"value": total * args.steps / t_plain, "unit": UNIT,
+            "plain": {"value": u_plain / t_plain, "unit": UNIT,
                       "what": "each box stepped by its own le_step, one after another"},
             "batched_over_plain": t_plain / t_batch,
             "autotune": {"force_threads": tf, "list_threads": tl, "seconds": t_tune,
                          "trial_ms_per_step": tms,
-                         "untuned_value": total * args.steps / t_untuned},
+                         "untuned_value": u_untuned / t_untuned},
             "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16,
                                "what": "plain vs batched and vs autotuned batched"}}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     b.close()
     bt.close()
     for s in plain + batched + tuned:
         s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
