@@ -51,6 +51,9 @@ def parse():
                          "256 uneven LJ boxes stepped alone vs in one batch; served: the "
                          "shear-sweep request stream with continuous batching")
     ap.add_argument("--systems", type=int, default=256, help="batched workload: box count")
+    ap.add_argument("--arrival-rate", type=float, default=50.0,
+                    help="served workload: request arrivals per second (the trace's 50/s "
+                         "arrival times stretched or compressed)")
     ap.add_argument("--particles", type=int, default=4194304,
                     help="box size (the default is the benchmark workload; smaller boxes "
                          "of the same density are for profiler captures)")

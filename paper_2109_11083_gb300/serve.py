@@ -242,8 +242,9 @@ def main_bench(args) -> int:
     count = 200
     steps = max(args.steps // 4, 50)
     reqs = trace_requests(count, steps)
+    rate = float(getattr(args, "arrival_rate", 50.0))
     srv = Server(budget_bytes=150 * 2 ** 30, quantum=100)
-    res = srv.run(reqs)
+    res = srv.run(reqs, time_scale=50.0 / rate)
     srv.close()
     lat = np.array([r.latency for r in res])
     wait = np.array([r.wait for r in res])
@@ -251,8 +252,8 @@ def main_bench(args) -> int:
     line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": 1, "steps": steps, "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"served_{count}_requests_poisson50_lj_kg_fp32",
-                       "requests": count, "steps_per_request": steps, "arrival_rate_per_s": 50,
+            "config": {"workload": f"served_{count}_requests_poisson{rate:g}_lj_kg_fp32",
+                       "requests": count, "steps_per_request": steps, "arrival_rate_per_s": rate,
                        "particles_per_request": [int(min(r.n for r in reqs)),
                                                  int(max(r.n for r in reqs))],
                        "budget_bytes": 150 * 2 ** 30, "quantum_steps": 100},
@@ -261,6 +262,6 @@ def main_bench(args) -> int:
             "wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
             "max_queue": srv.max_queue, "makespan_s": srv.elapsed,
             "offered_particle_steps_per_s": float(sum(r.n * r.steps for r in reqs) /
-                                                  max(r.arrival for r in reqs))}
+                                                  (max(r.arrival for r in reqs) * 50.0 / rate))}
     print(json.dumps(line), flush=True)
     return 0
