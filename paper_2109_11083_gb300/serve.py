@@ -143,6 +143,7 @@ class Server:
         self.used = 0
         self.particle_steps = 0
         self.max_queue = 0
+        self.time_scale = 1.0
 
     def _admit(self, req: Request, now: float) -> bool:
         need = request_bytes(req)
@@ -168,11 +169,13 @@ class Server:
         self.used -= lv.bytes
         r = lv.req
         eta = xz / r.shear_rate if r.shear_rate != 0 else float("nan")
-        return Result(r.id, now - r.arrival, lv.admitted - r.arrival, r.n, r.steps, eta, prof, cnt)
+        arrival = r.arrival * self.time_scale  # on the wall clock of this run
+        return Result(r.id, now - arrival, lv.admitted - arrival, r.n, r.steps, eta, prof, cnt)
 
     def run(self, requests: list[Request], time_scale: float = 1.0) -> list[Result]:
         """Serves the requests; arrival times are scaled by time_scale (wall
         clock).  Returns the results in completion order."""
+        self.time_scale = float(time_scale)
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque[Request] = collections.deque()
         results: list[Result] = []

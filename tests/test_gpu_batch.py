@@ -112,3 +112,31 @@ def test_mixed_groups_equal_alone_bitwise():
         assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 0
     for s in alone + mixed:
         s.close()
+
+
+def test_members_with_one_and_two_sort_passes_equal_alone_bitwise():
+    """Boxes small enough for a one-pass radix sort of their cell keys and
+    large enough to need two (over 512 cells), in one batch launch."""
+    specs = [{"n": n, "rho": 0.8442, "shear_rate": gd, "seed": 400 + k}
+             for k, (n, gd) in enumerate([(700, 0.9), (20000, 0.05), (1500, 0.3),
+                                          (26000, 0.2)])]
+    alone = [_box(s, 1) for s in specs]
+    mixed = [_box(s, 1) for s in specs]
+    passes = []
+    for a in alone:
+        c = a.counters()
+        ncell = c["cells"][0] * c["cells"][1] * c["cells"][2]
+        passes.append(1 if ncell <= 512 else 2)
+        a.step(40)
+    assert set(passes) == {1, 2}
+    with le.Batch() as b:
+        for m in mixed:
+            b.add(m)
+        b.step(40)
+    for a, m in zip(alone, mixed):
+        ra, va = a.positions()
+        rm, vm = m.positions()
+        assert np.array_equal(ra, rm) and np.array_equal(va, vm)
+        assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 0
+    for s in alone + mixed:
+        s.close()
