@@ -130,7 +130,8 @@ struct VBlock {
 
 // ------------------------------------------------------------------ k_drift
 template <class R>
-__device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, int bx) {
+__device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                           Bufs<R> s1, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = bx * blockDim.x + threadIdx.x;
   // time since the build at the step this drift produces
@@ -179,7 +180,8 @@ __device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bu
   }
 }
 template <class R>
-__global__ void __launch_bounds__(kDriftThreads) k_drift(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1) {
+__global__ void __launch_bounds__(kDriftThreads) k_drift(const __grid_constant__ Geom g,
+                                                         Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1) {
   drift_body<R>(g, d, s0, s1, (int)blockIdx.x);
 }
 
@@ -209,7 +211,8 @@ __device__ __forceinline__ void cross_window(const Geom &g, double fb, Dyn *d) {
 // One block.  Folds the previous step's fixed-point samples into the running
 // sums, advances the step, evaluates the rebuild trigger and fills the slot
 // offset table.
-__device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond, int bx) {
+__device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, Work w,
+                                            cudaGraphConditionalHandle h, int use_cond, int bx) {
   __shared__ double s_sh;
   __shared__ int need_sh;
   const int t = threadIdx.x;
@@ -305,7 +308,8 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
     }
   }
 }
-__global__ void __launch_bounds__(128) k_decide(const __grid_constant__ Geom g, Dyn *__restrict__ d, Work w, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(128) k_decide(const __grid_constant__ Geom g, Dyn *__restrict__ d,
+                                                Work w, cudaGraphConditionalHandle h, int use_cond) {
   decide_body(g, d, w, h, use_cond, (int)blockIdx.x);
 }
 
@@ -365,7 +369,8 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -544,14 +549,16 @@ __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V
 // DPD: the kicked half-step velocities, held back while k_force still read
 // the old ones of the neighbours, become the particles' velocities.
 template <class R>
-__device__ __forceinline__ void vcopy_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
+__device__ __forceinline__ void vcopy_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                           Bufs<R> s1, Work w, int bx) {
   const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const Bufs<R> &b = d->cur ? s1 : s0;
   b.v[i] = reinterpret_cast<const V4<R> *>(w.vnew)[i];
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_vcopy(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+__global__ void __launch_bounds__(256) k_vcopy(const __grid_constant__ Geom g, Dyn *__restrict__ d,
+                                               Bufs<R> s0, Bufs<R> s1, Work w) {
   vcopy_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
@@ -560,7 +567,8 @@ __global__ void __launch_bounds__(256) k_vcopy(const __grid_constant__ Geom g, D
 // two-stage shared-memory ring filled by bulk copies, and gathers neighbour
 // positions four at a time.
 template <class R, bool BONDS, bool DPD, class BX>
-__device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode, BX bx) {
+__device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, Bufs<R> s0,
+                                           Bufs<R> s1, Work w, int mode, BX bx) {
   __shared__ long long s_red[2][kForceWarps];
   __shared__ __align__(128) uint32_t s_rows[kForceWarps][2][kRowsPerChunk][32];
   __shared__ __align__(8) uint64_t s_bar[kForceWarps][2];
@@ -896,7 +904,8 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   }
 }
 template <class R, bool BONDS, bool DPD>
-__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode) {
+__global__ void __launch_bounds__(kForceThreads, (DPD || sizeof(R) == 8) ? 2 : LE_FORCE_MINB32) k_force(
+    const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int mode) {
   force_body<R, BONDS, DPD>(g, d, s0, s1, w, mode, HwBlock{});
 }
 
@@ -944,7 +953,8 @@ __device__ __forceinline__ int wrap_index(int c, int n) {
 // removed, x -= dX as m_b cells + f_b, vx -= shear_rate*Lz), periodic x/y.
 // Writes the new displacement (pre-sort order) and the sort keys/values.
 template <class R>
-__device__ __forceinline__ void rb_bin_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int bx) {
+__device__ __forceinline__ void rb_bin_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                            Bufs<R> s1, Work w, int bx) {
   const Bufs<R> b = pick(d->cur, s0, s1);
   const int i = bx * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
@@ -995,7 +1005,8 @@ __device__ __forceinline__ void rb_bin_body(const Geom g, Dyn *__restrict__ d, B
   if constexpr (sizeof(R) == 4) w.tmp_lo[i] = make_float4(u.l[0], u.l[1], u.l[2], 0.f);
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bin(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
+__global__ void __launch_bounds__(256) k_rb_bin(const __grid_constant__ Geom g, Dyn *__restrict__ d,
+                                                Bufs<R> s0, Bufs<R> s1, Work w) {
   rb_bin_body<R>(g, d, s0, s1, w, (int)blockIdx.x);
 }
 
@@ -1049,7 +1060,10 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
 // Gathers the re-based state into cell order.  Forces are not moved: the
 // pair kernel of the same step overwrites them before anything reads them.
 template <class R>
-__device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval, int bx) {
+__device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                                Bufs<R> s1, Work w,
+                                                const uint32_t *__restrict__ skey,
+                                                const uint32_t *__restrict__ sval, int bx) {
   const int cur = d->cur;
   const Bufs<R> src = pick(cur, s0, s1);
   const Bufs<R> dst = pick(1 - cur, s0, s1);
@@ -1085,13 +1099,17 @@ __device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ 
   }
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_permute(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, const uint32_t *__restrict__ skey, const uint32_t *__restrict__ sval) {
+__global__ void __launch_bounds__(256) k_rb_permute(const __grid_constant__ Geom g,
+                                                    Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1,
+                                                    Work w, const uint32_t *__restrict__ skey,
+                                                    const uint32_t *__restrict__ sval) {
   rb_permute_body<R>(g, d, s0, s1, w, skey, sval, (int)blockIdx.x);
 }
 
 // ----------------------------------------------------------- rebuild: ranges
 // cell_start[c] = first sorted slot of cell c (every entry written once).
-__device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start, int bx) {
+__device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__restrict__ skey,
+                                               int *__restrict__ cell_start, int bx) {
   const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int c = min((int)skey[k], g.ncell - 1);
@@ -1100,7 +1118,9 @@ __device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__r
   if (k == g.n - 1)
     for (int cc = c + 1; cc <= g.ncell; ++cc) cell_start[cc] = g.n;
 }
-__global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom g, const uint32_t *__restrict__ skey, int *__restrict__ cell_start) {
+__global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom g,
+                                                   const uint32_t *__restrict__ skey,
+                                                   int *__restrict__ cell_start) {
   rb_ranges_body(g, skey, cell_start, (int)blockIdx.x);
 }
 
@@ -1150,7 +1170,8 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 // (f_build/lx decides whether the window reaches a 4th cell).  Rows and
 // cells whose box lies farther than rl from the particle are skipped.
 template <class R, class BX>
-__device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, BX bx) {
+__device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                             Bufs<R> s1, Work w, int target_cur, BX bx) {
   __shared__ float s_offx[kNumSlots];
   for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
   __syncthreads();
@@ -1234,7 +1255,9 @@ __device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, 
   }
 }
 template <class R>
-__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+__global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(
+    const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w,
+    int target_cur) {
   rb_list_body<R>(g, d, s0, s1, w, target_cur, HwBlock{});
 }
 
@@ -1242,7 +1265,8 @@ __global__ void __launch_bounds__(kListMaxThreads, LE_LIST_MINB) k_rb_list(const
 // Slot of every bond: its LE minimum image at the build (FP64), expressed as
 // build-cell offset + image, then matched to the 90-slot table.
 template <class R>
-__device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur, int bx) {
+__device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                              Bufs<R> s1, Work w, int target_cur, int bx) {
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int k = bx * blockDim.x + threadIdx.x;
@@ -1288,7 +1312,9 @@ __device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d,
   }
 }
 template <class R>
-__global__ void __launch_bounds__(256) k_rb_bonds(const __grid_constant__ Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w, int target_cur) {
+__global__ void __launch_bounds__(256) k_rb_bonds(const __grid_constant__ Geom g,
+                                                  Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1,
+                                                  Work w, int target_cur) {
   rb_bonds_body<R>(g, d, s0, s1, w, target_cur, (int)blockIdx.x);
 }
 

@@ -20,7 +20,9 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
-__device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, int n, int shift, int bits, int nblocks, uint32_t *__restrict__ hist, int bx) {
+__device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, int n, int shift,
+                                             int bits, int nblocks, uint32_t *__restrict__ hist,
+                                             int bx) {
   __shared__ uint32_t cnt[kSortBuckets];
   const int nb = 1 << bits;
   const uint32_t mask = (uint32_t)nb - 1u;
@@ -35,7 +37,9 @@ __device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, i
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(size_t)b * nblocks + bx] = cnt[b];
 }
-__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__restrict__ key, int n, int shift, int bits, int nblocks, uint32_t *__restrict__ hist) {
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t *__restrict__ key, int n,
+                                                          int shift, int bits, int nblocks,
+                                                          uint32_t *__restrict__ hist) {
   rs_hist_body(key, n, shift, bits, nblocks, hist, (int)blockIdx.x);
 }
 
@@ -63,7 +67,8 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *warp_t
 }
 
 // Pass 1 of the scan: the sum of each chunk of kScanChunk counts.
-__device__ __forceinline__ void scan_sums_body(const uint32_t *__restrict__ a, int m, uint32_t *__restrict__ part, int bx) {
+__device__ __forceinline__ void scan_sums_body(const uint32_t *__restrict__ a, int m,
+                                               uint32_t *__restrict__ part, int bx) {
   __shared__ uint32_t wt[32];
   const int base = bx * kScanChunk + threadIdx.x * kScanItems;
   uint32_t s = 0;
@@ -73,7 +78,8 @@ __device__ __forceinline__ void scan_sums_body(const uint32_t *__restrict__ a, i
   const uint32_t incl = block_incl_scan(s, wt);
   if (threadIdx.x == kScanThreads - 1) part[bx] = incl;
 }
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t *__restrict__ a, int m, uint32_t *__restrict__ part) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t *__restrict__ a, int m,
+                                                            uint32_t *__restrict__ part) {
   scan_sums_body(a, m, part, (int)blockIdx.x);
 }
 
@@ -99,7 +105,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict_
 }
 
 // Pass 3: exclusive scan inside each chunk, offset by the chunk's start.
-__device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part, int bx) {
+__device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m,
+                                                const uint32_t *__restrict__ part, int bx) {
   __shared__ uint32_t wt[32];
   const int base = bx * kScanChunk + threadIdx.x * kScanItems;
   uint32_t v[kScanItems], s = 0;
@@ -115,11 +122,17 @@ __device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m,
     run += v[k];
   }
 }
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(
+    uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part) {
   scan_apply_body(a, m, part, (int)blockIdx.x);
 }
 
-__device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks, const uint32_t *__restrict__ hist, int bx) {
+__device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin,
+                                                const uint32_t *__restrict__ vin,
+                                                uint32_t *__restrict__ kout,
+                                                uint32_t *__restrict__ vout, int n, int shift,
+                                                int bits, int nblocks,
+                                                const uint32_t *__restrict__ hist, int bx) {
   __shared__ uint32_t base[kSortBuckets];          // global start of each digit for this tile
   __shared__ uint32_t wcnt[kWarps][kSortBuckets];  // per-warp counts -> per-warp offsets
   __shared__ uint32_t total[kSortBuckets];
@@ -169,7 +182,10 @@ __device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin
     __syncthreads();
   }
 }
-__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks, const uint32_t *__restrict__ hist) {
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int n, int shift, int bits, int nblocks,
+    const uint32_t *__restrict__ hist) {
   rs_scatter_body(kin, vin, kout, vout, n, shift, bits, nblocks, hist, (int)blockIdx.x);
 }
 
@@ -200,7 +216,8 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_sums(const MemberDev<R> 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *__restrict__ mem, int p) {
+__global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *__restrict__ mem,
+                                                            int p) {
   const MemberDev<R> &q = mem[blockIdx.x];
   if (!q.d->rebuild || p >= q.sort_passes) return;
   int shift, w;
