@@ -51,6 +51,9 @@ def parse():
                          "256 uneven LJ boxes stepped alone vs in one batch; served: the "
                          "shear-sweep request stream with continuous batching")
     ap.add_argument("--systems", type=int, default=256, help="batched workload: box count")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batched workload: time the batch alone (no per-box comparison, "
+                         "no tuning), for profiler captures")
     ap.add_argument("--arrival-rate", type=float, default=50.0,
                     help="served workload: request arrivals per second (the trace's 50/s "
                          "arrival times stretched or compressed)")
@@ -400,8 +403,9 @@ def run_batched(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-    plain = [make_box_sim(le, s) for s in specs]
-    batched = [make_box_sim(le, s) for s in specs]
+    compare = not args.no_plain
+    plain = [make_box_sim(le, s) for s in specs] if compare else []
+    batched = [make_box_sim(le, s) for s in specs] if compare else []
     tuned = [make_box_sim(le, s) for s in specs]
     w = max(args.warmup, 3)
     for s in plain:
@@ -409,7 +413,8 @@ def run_batched(args):
     b = le.Batch()
     for s in batched:
         b.add(s)
-    b.step(w)
+    if compare:
+        b.step(w)
     # the same boxes once more, launch shapes picked by the autotuner on the
     # whole batch (the trials are rolled back, so these members stay on the
     # same trajectories)
@@ -419,7 +424,7 @@ def run_batched(args):
     bt.step(w)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tf, tl, tms = bt.tune(32)
+    tf, tl, tms = bt.tune(32) if compare else (None, None, None)
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t0
     barrier()
@@ -429,7 +434,8 @@ def run_batched(args):
     barrier()
     t_plain = time.perf_counter() - t0
     t0 = time.perf_counter()
-    b.step(args.steps)
+    if compare:
+        b.step(args.steps)
     barrier()
     t_untuned = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -440,7 +446,7 @@ def run_batched(args):
     t_untuned, u_untuned = job_totals(t_untuned, total * args.steps)
     t_batch, u_batch = job_totals(t_batch, total * args.steps)
     equal = True
-    for k in range(0, len(specs), max(1, len(specs) // 16)):
+    for k in range(0, len(plain), max(1, len(plain) // 16)):
         rp, vp = plain[k].positions()
         for other in (batched[k], tuned[k]):
             rb, vb = other.positions()
@@ -461,13 +467,15 @@ def run_batched(args):
                        "density_range": [0.7, 0.9], "shear_range": [1e-3, 1.0], "rc": 2.5,
                        "skin": 0.3, "dt": 0.005},
             "plain": {"value": u_plain / t_plain, "unit": UNIT,
-                      "what": "each box stepped by its own le_step, one after another"},
-            "batched_over_plain": t_plain / t_batch,
+                      "what": "each box stepped by its own le_step, one after another"}
+            if compare else None,
+            "batched_over_plain": t_plain / t_batch if compare else None,
             "autotune": {"force_threads": tf, "list_threads": tl, "seconds": t_tune,
                          "trial_ms_per_step": tms,
-                         "untuned_value": u_untuned / t_untuned},
+                         "untuned_value": u_untuned / t_untuned} if compare else None,
             "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16,
-                               "what": "plain vs batched and vs autotuned batched"}}
+                               "what": "plain vs batched and vs autotuned batched"}
+            if compare else None}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
