@@ -46,11 +46,13 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels without CUDA graphs (for profilers that cannot see "
                          "kernels inside conditional graphs)")
-    ap.add_argument("--workload", default="box", choices=["box", "batched", "served"],
+    ap.add_argument("--workload", default="box", choices=["box", "batched", "served", "kg"],
                     help="box: the 4,194,304-particle LJ box (the benchmark line); batched: "
                          "256 uneven LJ boxes stepped alone vs in one batch; served: the "
                          "shear-sweep request stream with continuous batching")
     ap.add_argument("--systems", type=int, default=256, help="batched workload: box count")
+    ap.add_argument("--angle-k", type=float, default=0.0,
+                    help="kg workload: bending constant k_a of Eq. 12 (0: WCA + FENE only)")
     ap.add_argument("--no-plain", action="store_true",
                     help="batched workload: time the batch alone (no per-box comparison, "
                          "no tuning), for profiler captures")
@@ -487,12 +489,83 @@ def run_batched(args):
     return 0
 
 
+def le_min_image(d, box, dX):
+    """Lees-Edwards minimum image of separations d (n x 3) in a cubic box."""
+    d = d.copy()
+    up, dn = d[:, 2] > 0.5 * box, d[:, 2] < -0.5 * box
+    d[up, 2] -= box
+    d[up, 0] -= dX
+    d[dn, 2] += box
+    d[dn, 0] += dX
+    d[:, :2] -= box * np.rint(d[:, :2] / box)
+    return d
+
+
+def run_kg(args):
+    """Config 2: a Kremer-Grest melt of 200 chains x 100 beads (WCA + FENE,
+    optional Eq. 12 bending with --angle-k), FP32 forces, dt 0.01, shear rate
+    1e-3, Langevin xi 0.5.  The chains start on a serpentine lattice path at
+    the bead density 0.85 (bond 1.02, no overlaps), so no push-off is needed."""
+    import torch
+    import paper_2109_11083_gb300 as le
+    torch.cuda.set_device(0)
+    w = synth.kg_melt_200x100()
+    k = math.ceil(w.n ** (1 / 3) - 1e-9)
+    pos, box, bonds = synth.lattice_chains(w.nchains, w.nbeads, w.rho * k ** 3 / w.n, w.seed)
+    vel = synth.mb_velocities(w.n, w.kT, w.seed)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * box)
+    stream = torch.cuda.current_stream()
+    sim = le.Sim(box, w.shear_rate, w.rc, w.skin, stream=stream.cuda_stream, dt=w.dt, xi=w.xi,
+                 kT=w.kT, fene_k=w.fene_k, fene_R0=w.fene_R0, seed=w.seed, system_id=1,
+                 precision=le.LE_FP32, sample_every=1, angle_k=args.angle_k)
+    sim.set_bonds(bonds)
+    sim.set_particles(pos, vel)
+    sim.step(max(args.warmup, 3))
+    tuned = sim.tune(64)
+    sim.reset_samples()
+    c0 = sim.counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c1 = sim.counters()
+    r, _ = sim.positions()
+    d = le_min_image(r[bonds[:, 1]] - r[bonds[:, 0]], box, c1["dX"])
+    ree = d.reshape(w.nchains, w.nbeads - 1, 3).sum(axis=1)
+    _, xz, nsamp = sim.stress(instantaneous=False)
+    line = {"metric": METRIC, "value": w.n * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_beads": w.n, "chains": w.nchains,
+                       "beads_per_chain": w.nbeads, "density": w.rho, "box": round(box, 6),
+                       "rc": w.rc, "skin": w.skin, "fene_k": w.fene_k, "fene_R0": w.fene_R0,
+                       "angle_k": args.angle_k, "shear_rate": w.shear_rate, "dt": w.dt,
+                       "langevin_xi": w.xi, "kT": w.kT, "start": "serpentine lattice path",
+                       "launch_shapes": {"force_threads": tuned[0], "list_threads": tuned[1]}},
+            "rebuilds": c1["rebuilds"] - c0["rebuilds"],
+            "chains": {"R_ee2_mean": float((ree ** 2).sum(axis=1).mean()),
+                       "bond_mean": float(np.linalg.norm(d, axis=1).mean()),
+                       "what": "from the LE minimum-image bond vectors after the timed steps"},
+            "viscosity_short_run": {"eta": xz / w.shear_rate, "samples": nsamp,
+                                    "what": "<sigma_xz>/shear_rate over the timed steps only "
+                                            "(far too short for a converged value at 1e-3)"}}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "kg":
+        return run_kg(args)
     if args.workload == "served":
         from paper_2109_11083_gb300 import serve
         return serve.main_bench(args)
