@@ -140,3 +140,31 @@ def test_members_with_one_and_two_sort_passes_equal_alone_bitwise():
         assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 0
     for s in alone + mixed:
         s.close()
+
+
+def test_a_member_error_rolls_every_member_back():
+    """One member breaks a FENE bond (two bonded beads flying apart): the batch
+    call reports it and every member is back at its state before the call."""
+    specs = synth.batched_systems(count=3, nmin=800, nmax=2000, seed=17)
+    good = [_box(s, 1) for s in specs]
+    pos = np.array([[2.0, 2.0, 2.0], [3.0, 2.0, 2.0], [5.0, 5.0, 5.0]])
+    vel = np.array([[-30.0, 0, 0], [30.0, 0, 0], [0, 0, 0]])
+    bad = le.Sim(10.0, 0.0, 2 ** (1 / 6), 0.3, thermostat=0, dt=0.01, precision=1)
+    bad.set_bonds([[0, 1]])
+    bad.set_particles(pos, vel)
+    with le.Batch() as b:
+        for s in good:
+            b.add(s)
+        b.step(10)
+        b.add(bad)
+        before = [s.positions() for s in good + [bad]]
+        steps0 = [s.counters()["step"] for s in good + [bad]]
+        with pytest.raises(le.LEError) as e:
+            b.step(50)
+        assert e.value.status == 5
+        for s, (r0, v0), n0 in zip(good + [bad], before, steps0):
+            r1, v1 = s.positions()
+            assert np.array_equal(r0, r1) and np.array_equal(v0, v1)
+            assert s.counters()["step"] == n0
+    for s in good + [bad]:
+        s.close()
