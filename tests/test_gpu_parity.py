@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (called through the C ABI) against the FP64 CPU
 oracle on the same seeded inputs.
 
-Tolerances.  FP64 mode: the benchmark spec's bounds, per-step forces within a
+Tolerances.  FP64 mode: per-step forces within a
 relative 1e-5 (global L2 and per particle against max(|F_i|, <|F|>)) and
 10-step positions within 1e-4.  FP32 mode: forces come from FP32
 cell-relative coordinates, so each particle's force must lie within the
