@@ -384,7 +384,7 @@ def make_box_sim(le, spec, stream=None):
 
 
 def run_batched(args):
-    """Config 4: independent LJ boxes of uneven N stepped one handle at a time
+    """256 independent LJ boxes of uneven N (500 to 32,000) stepped one handle at a time
     (plain) and all together in one batch, equal accuracy checked bitwise."""
     import torch
     rank, world, local = dist_info()
@@ -502,7 +502,7 @@ def le_min_image(d, box, dX):
 
 
 def run_kg(args):
-    """Config 2: a Kremer-Grest melt of 200 chains x 100 beads (WCA + FENE,
+    """A Kremer-Grest melt of 200 chains x 100 beads (WCA + FENE,
     optional Eq. 12 bending with --angle-k), FP32 forces, dt 0.01, shear rate
     1e-3, Langevin xi 0.5.  The chains start on a serpentine lattice path at
     the bead density 0.85 (bond 1.02, no overlaps), so no push-off is needed."""
