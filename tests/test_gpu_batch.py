@@ -10,13 +10,13 @@ le = pytest.importorskip("paper_2109_11083_gb300")
 pytestmark = pytest.mark.gpu
 
 
-def _box(spec, prec):
+def _box(spec, prec, bins=8):
     pos, box = synth.lj_box(spec["n"], spec["rho"], spec["seed"])
     vel = synth.mb_velocities(spec["n"], 1.0, spec["seed"])
     gd = spec["shear_rate"]
     vel[:, 0] += gd * (pos[:, 2] - 0.5 * box)
     sim = le.Sim(box, gd, 2.5, 0.3, seed=spec["seed"], system_id=spec["seed"], precision=prec,
-                 profile_bins=8)
+                 profile_bins=bins)
     sim.set_particles(pos, vel)
     return sim
 
@@ -93,7 +93,8 @@ def test_mixed_groups_equal_alone_bitwise():
     specs = synth.batched_systems(count=3, nmin=800, nmax=4000, seed=81)
 
     def make():
-        return ([_box(s, p) for s, p in zip(specs, (1, 0, 1))] +
+        # profile bin counts differ between members of one launch group
+        return ([_box(s, p, b) for s, p, b in zip(specs, (1, 0, 1), (8, 8, 40))] +
                 [_kg(31, 1), _kg(32, 0), _dpd(33, 1), _dpd(34, 0)])
 
     alone, mixed = make(), make()
@@ -110,6 +111,8 @@ def test_mixed_groups_equal_alone_bitwise():
         assert np.array_equal(a.forces(), m.forces())
         assert a.stress(instantaneous=False)[1] == m.stress(instantaneous=False)[1]
         assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 0
+        for x, y in zip(a.profiles(), m.profiles()):
+            assert np.array_equal(x, y, equal_nan=True)
     for s in alone + mixed:
         s.close()
 
