@@ -115,6 +115,10 @@ def lib():
             L.ora_force_error_bound.restype = None
             L.ora_force_error_bound.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
                                                 C.c_int64, _I32, C.c_double, C.c_double, _D]
+            L.ora_band_pairs.restype = C.c_int64
+            L.ora_band_pairs.argtypes = [C.POINTER(Params), C.c_double, C.c_int64, _D,
+                                         C.c_double, C.c_int64, C.POINTER(C.c_int64), _D,
+                                         _I32]
             L.ora_observe.restype = C.c_int
             L.ora_observe.argtypes = [C.POINTER(Params), C.c_int64, C.c_int64, _D, _D,
                                       C.c_int64, _I32, C.c_int, _D, _D, _D]
@@ -220,6 +224,25 @@ def force_error_bound(p: Params, dx_offset: float, pos, bonds=None, u: float = 2
     lib().ora_force_error_bound(C.byref(p), dx_offset, pos.shape[0], _dp(pos), b.shape[0],
                                 b.ctypes.data_as(_I32), u, P, _dp(B))
     return B
+
+
+def band_pairs(p: Params, dx_offset: float, pos, band: float):
+    """Ordered pairs within `band` of the LJ cut-off (|r - rc| <= band).
+
+    Returns (ij (m,2) int64, pair force F_ij on i (m,3), inside (m,) bool:
+    whether the oracle's strict r < rc test counts the pair)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cap = 64
+    while True:
+        ij = np.zeros((cap, 2), dtype=np.int64)
+        f = np.zeros((cap, 3))
+        inside = np.zeros(cap, dtype=np.int32)
+        m = lib().ora_band_pairs(C.byref(p), dx_offset, pos.shape[0], _dp(pos), band, cap,
+                                 ij.ctypes.data_as(C.POINTER(C.c_int64)), _dp(f),
+                                 inside.ctypes.data_as(_I32))
+        if m <= cap:
+            return ij[:m], f[:m], inside[:m].astype(bool)
+        cap = int(m)
 
 
 class State:

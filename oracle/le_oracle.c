@@ -508,6 +508,55 @@ void ora_force_error_bound(const ora_params *p, double dX, int64_t n, const doub
     free(c.m);
 }
 
+/* The pairs a reduced-precision evaluation may legitimately decide either
+ * way: every ordered pair (i, j) whose LE minimum-image distance lies within
+ * `band` of the strict cut-off of Eq. 9/10 (|r - rc| <= band).  For each, the
+ * pair force F_ij = f(r) d at its FP64 separation, and whether ora_forces
+ * counts it (r < rc).  Writes at most `cap` pairs and returns how many there
+ * are.  Test infrastructure: lets a comparison take either decision for such
+ * a pair and count the pairs decided the other way. */
+typedef struct {
+    const ora_params *p;
+    double dX, band;
+    const double *pos;
+    int64_t cap, count;
+    int64_t *ij;
+    double *f;
+    int32_t *inside;
+} band_ctx;
+
+static void band_visit(void *vctx, int64_t i, int64_t j)
+{
+    band_ctx *c = (band_ctx *)vctx;
+    double d[3];
+    ora_min_image(c->p, c->dX, c->pos + 3 * i, c->pos + 3 * j, d);
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double rc = c->p->rc;
+    if (!(fabs(r - rc) <= c->band)) return;
+    if (c->count < c->cap) {
+        double e, fr = lj_f_over_r(c->p, r * r, &e);
+        int64_t k = c->count;
+        c->ij[2 * k] = i;
+        c->ij[2 * k + 1] = j;
+        for (int a = 0; a < 3; ++a) c->f[3 * k + a] = fr * d[a];
+        c->inside[k] = (r * r < rc * rc) ? 1 : 0;
+    }
+    c->count += 1;
+}
+
+int64_t ora_band_pairs(const ora_params *p, double dX, int64_t n, const double *pos,
+                       double band, int64_t cap, int64_t *ij, double *f, int32_t *inside)
+{
+    band_ctx c;
+    c.p = p; c.dX = dX; c.band = band; c.pos = pos;
+    c.cap = cap; c.count = 0; c.ij = ij; c.f = f; c.inside = inside;
+    if (p->eps == 0.0) return 0;
+    ora_params q = *p;   /* a grid edge of rc + band covers every pair in the band */
+    q.rc = p->rc + band;
+    for_candidates(&q, n, pos, 1, &c, band_visit);
+    return c.count;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Eqs. 6-8, the DPD thermostat: pairwise dissipative and random forces for
  * r < rc.  As printed both carry |r^.v_ij| and the random force has no

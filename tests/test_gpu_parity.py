@@ -1,15 +1,19 @@
 """GPU parity: the CUDA path (called through the C ABI) against the FP64 CPU
 oracle on the same seeded inputs.
 
-Tolerances.  FP64 mode: per-step forces within a
-relative 1e-5 (global L2 and per particle against max(|F_i|, <|F|>)) and
-10-step positions within 1e-4.  FP32 mode: forces come from FP32
-cell-relative coordinates, so each particle's force must lie within the
-first-order rounding bound B_i that the oracle derives from the arithmetic
-(oracle.force_error_bound: separation error u(6P + 2r) per component with
-u = 2^-24 and P the largest reference-relative coordinate, times the norm of
-dF/dd, plus evaluation and summation rounding), and the L2 error over all
-particles within the L2 norm of B.
+Tolerances.  Both precisions: per-step forces within a relative 1e-5 (global
+L2 over all components, and per particle against max(|F_i|, <|F|>)) and
+10-step positions within 1e-4.  In FP32 mode a pair whose distance lies within
+the rounding band of the strict cut-off (|r - rc| <= 4 sqrt(3) u (6P + 2 rc),
+u = 2^-24, P the largest reference-relative coordinate) may be counted or not:
+either is a correct FP32 result, so the comparison takes the FP32 path's
+decision for those pairs (oracle.band_pairs) and reports how many it took the
+other way instead of counting them as error.  Each particle's FP32 force error
+must in addition lie within the first-order rounding bound B_i that the oracle
+derives from the arithmetic (oracle.force_error_bound: separation error
+u(6P + 2r) per component times the norm of dF/dd, plus evaluation and
+summation rounding, plus the whole pair force of band pairs), and the L2 error
+over all particles within the L2 norm of B.
 """
 import math
 
@@ -18,15 +22,26 @@ import pytest
 
 import oracle
 import synth
-from helpers import force_errors, le_delta
+from helpers import flip_resolved_errors, force_errors, le_delta
 
 le = pytest.importorskip("paper_2109_11083_gb300")
 
 pytestmark = pytest.mark.gpu
 
-FP64_FORCE_TOL = 1e-5
+FORCE_TOL = 1e-5
+FP64_FORCE_TOL = FORCE_TOL
 POS_TOL = 1e-4
 U32 = 2.0 ** -24
+# worst FP32 errors seen by the tests of this module (flip-resolved), printed
+# at the end of each FP32 test
+FP32_SEEN = {"l2": 0.0, "particle": 0.0, "flips": 0, "band": 0}
+
+
+def band_width(P, rc):
+    """Distance from the cut-off within which an FP32 separation may fall on
+    either side of the strict r < rc test (four times the first-order
+    separation bound, so that no flip escapes the comparison)."""
+    return 4.0 * math.sqrt(3.0) * U32 * (6.0 * P + 2.0 * rc)
 
 
 def lj_inputs(n, rho, gd, seed, kT=1.0, jitter=0.0):
@@ -61,15 +76,24 @@ def ref_extent(box, rc, skin, bonds=None):
     return 0.5 * lc + 0.5 * skin
 
 
-def assert_forces(f, ref, prec, what="", bound=None):
+def assert_forces(f, ref, prec, what="", bound=None, band=None, rows=None):
+    """FP64: the benchmark spec's tolerance directly.  FP32: the same tolerance once
+    the band pairs' cut-off decisions are taken out (band = oracle.band_pairs
+    output), and every particle within the rounding bound."""
     g, q = force_errors(f, ref)
     if prec == 0:
         assert g <= FP64_FORCE_TOL and q <= FP64_FORCE_TOL, (what, g, q)
-    else:
-        err = np.linalg.norm(np.asarray(f) - np.asarray(ref), axis=1)
-        worst = int(np.argmax(err / bound))
-        assert np.all(err <= bound), (what, worst, err[worst], bound[worst])
-        assert np.linalg.norm(err) <= np.linalg.norm(bound), (what, g)
+        return g, q
+    err = np.linalg.norm(np.asarray(f) - np.asarray(ref), axis=1)
+    worst = int(np.argmax(err / bound))
+    assert np.all(err <= bound), (what, worst, err[worst], bound[worst])
+    assert np.linalg.norm(err) <= np.linalg.norm(bound), (what, g)
+    g, q, flips, nband = flip_resolved_errors(f, ref, *band, rows=rows)
+    FP32_SEEN["l2"] = max(FP32_SEEN["l2"], g)
+    FP32_SEEN["particle"] = max(FP32_SEEN["particle"], q)
+    FP32_SEEN["flips"] += flips
+    FP32_SEEN["band"] += nband
+    assert g <= FORCE_TOL and q <= FORCE_TOL, (what, g, q, flips)
     return g, q
 
 
@@ -80,10 +104,12 @@ def check_at_gpu_positions(sim, p, step, prec, box, rc, skin, bonds=None, use_ce
     dX = oracle.dX(p, step)
     st, F, _, _ = oracle.forces(p, dX, r, bonds, use_cells=use_cells)
     assert st == oracle.OK
-    B = None
+    B = band = None
     if prec == 1:
-        B = oracle.force_error_bound(p, dX, r, bonds, U32, ref_extent(box, rc, skin, bonds))
-    return assert_forces(sim.forces(), F, prec, f"step {step}", B)
+        P = ref_extent(box, rc, skin, bonds)
+        B = oracle.force_error_bound(p, dX, r, bonds, U32, P)
+        band = oracle.band_pairs(p, dX, r, band_width(P, rc))
+    return assert_forces(sim.forces(), F, prec, f"step {step}", B, band)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -310,7 +336,10 @@ def test_full_size_box_sampled_forces():
     # the rounding bound needs every pair of the sampled particles: take it
     # from the sampled particles' neighbourhood (a sub-box around each would
     # do; the full box is used once, with the cell list)
-    B = oracle.force_error_bound(p, dX, r, None, U32, ref_extent(w.box, w.rc, w.skin))[idx]
-    assert_forces(f[idx], F, 1, "full size", B)
+    P = ref_extent(w.box, w.rc, w.skin)
+    B = oracle.force_error_bound(p, dX, r, None, U32, P)[idx]
+    band = oracle.band_pairs(p, dX, r, band_width(P, w.rc))
+    assert_forces(f[idx], F, 1, "full size", B, band, rows=idx)
+    print(f"full size: FP32 errors (flip-resolved) {FP32_SEEN}")
     assert sim.counters()["rebuilds"] >= 1
     sim.close()

@@ -1,8 +1,10 @@
 """The allocation-free force entry point, le_forces_noalloc, for callers that
 cannot allocate device memory where they need forces: its output must equal
 the forces a handle computes for the same positions and step (le_forces),
-within the tolerances of the other GPU tests, on two calls in a row (the
-second reuses the static device array the first one left behind).
+and the FP64 oracle's forces, within the tolerances of the other GPU tests
+(relative 1e-5; in FP32 once the cut-off decisions of pairs within the
+rounding band of rc are taken out), on two calls in a row (the second reuses
+the static device array the first one left behind).
 
 Collected last on purpose (file name), so a run that stops at the first
 failure has already run every other test."""
@@ -13,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import force_errors
+from helpers import flip_resolved_errors, force_errors
 
 le = pytest.importorskip("paper_2109_11083_gb300")
 
@@ -41,14 +43,25 @@ def test_noalloc_forces_equal_handle_forces_twice(prec):
         r, _ = sim.positions()
         f_ref = sim.forces()
         f = le.le_forces_noalloc(box, gd, rc, skin, params, step, r)
+        p = oracle.params(box, gd, rc)
+        dX = oracle.dX(p, step)
+        st, F, _, _ = oracle.forces(p, dX, r)
+        assert st == oracle.OK
         if prec == 0:
             g, q = force_errors(f, f_ref)
             assert g <= 1e-5 and q <= 1e-5, (call, g, q)
+            g, q = force_errors(f, F)
+            assert g <= 1e-5 and q <= 1e-5, (call, g, q)
         else:
+            # against the oracle: the benchmark spec's tolerance once the band
+            # pairs' cut-off decisions are taken out
+            P = 0.5 * box / math.floor(box / (rc + skin))
+            band = 4.0 * math.sqrt(3.0) * 2.0 ** -24 * (6.0 * P + 2.0 * rc)
+            g, q, flips, _ = flip_resolved_errors(f, F, *oracle.band_pairs(p, dX, r, band))
+            assert g <= 1e-5 and q <= 1e-5, (call, g, q, flips)
             # both sides round positions to FP32 around different cell
             # references: each may differ from the exact forces by the
             # oracle's rounding bound, so together by twice that
-            p = oracle.params(box, gd, rc)
             edge = rc + skin
             P = 0.5 * box / math.floor(box / edge) + 0.5 * skin
             B = oracle.force_error_bound(p, oracle.dX(p, step), r, None, 2.0 ** -24, P)
