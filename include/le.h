@@ -28,8 +28,8 @@
  *
  * Errors: every call returns an le_status and never aborts.  le_last_error()
  * describes the last failure on a handle.  When le_step fails with
- * LE_ERR_BOND_BROKEN, LE_ERR_NONFINITE or LE_ERR_CAPACITY the state is rolled
- * back to what it was when that le_step call began.
+ * LE_ERR_BOND_BROKEN, LE_ERR_NONFINITE, LE_ERR_RANGE or LE_ERR_CAPACITY the
+ * state is rolled back to what it was when that le_step call began.
  */
 #ifndef LE_H
 #define LE_H
@@ -59,7 +59,9 @@ typedef enum le_status {
     LE_ERR_NONFINITE = 6,     /* a force or velocity became NaN or infinite */
     LE_ERR_CAPACITY = 7,      /* the neighbour list overflowed and could not grow */
     LE_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
-    LE_ERR_STATE = 9          /* call order: e.g. le_step before le_set_particles */
+    LE_ERR_STATE = 9,         /* call order: e.g. le_step before le_set_particles */
+    LE_ERR_RANGE = 10         /* a sampled |vx| > 1000 or m vy^2 > 2000: beyond the
+                                 fixed-point range of the profile sums */
 } le_status;
 
 typedef enum le_precision {
@@ -136,7 +138,10 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
 /* Advances nsteps >= 0 velocity-Verlet steps (kick, drift, LE wrap and
  * velocity jump, rebuild when the skin-displacement + image-shift trigger
  * fires, LJ/FENE forces under the LE minimum image, Langevin on the peculiar
- * velocity, kick, samples).  Returns when the work has finished. */
+ * velocity, kick, samples).  Returns when the work has finished.
+ * Errors (state rolled back to the start of the call): LE_ERR_BOND_BROKEN,
+ * LE_ERR_NONFINITE, LE_ERR_RANGE, LE_ERR_CAPACITY (after growing the list
+ * failed); also LE_ERR_STATE, LE_ERR_INVALID_ARG, LE_ERR_TIMEOUT, LE_ERR_CUDA. */
 LE_API le_status le_step(le_sim *s, int64_t nsteps);
 
 /* Conservative forces (LJ + FENE) of the current step, n x 3 row-major. */
@@ -294,15 +299,30 @@ LE_API const char *le_batch_last_error(const le_batch *b);
  * nothing: all of its device buffers are carved out of one static device
  * array of 32 MiB that every device loading this library holds until exit,
  * which bounds n to 16,384 (fewer for very dense boxes; LE_ERR_INVALID_ARG
- * beyond).  The first call on a device looks the array's address up; make it
- * before any stream capture.  Calls share the array, serialise on a lock and
+ * beyond).  The first call in each CUDA context of a device (its primary
+ * context, or a new one after a reset) looks the array's address up; make
+ * the first call on a device before any stream capture.  Calls share the array, serialise on a lock and
  * return after their device work (on cuda_stream, NULL for the default
  * stream) has finished; work that overlapped a call on the array would race.
  * Errors: LE_ERR_INVALID_ARG, LE_ERR_BOX_TOO_SMALL, LE_ERR_CAPACITY,
- * LE_ERR_NONFINITE, LE_ERR_CUDA. */
+ * LE_ERR_NONFINITE, LE_ERR_TIMEOUT (a bounded wait on a bulk copy in the
+ * pair kernel gave up), LE_ERR_CUDA. */
 LE_API le_status le_forces_noalloc(const double box[3], double shear_rate, double rc, double skin,
                                    const le_params *p, int64_t step, int64_t n, const double *pos,
                                    double *forces, void *cuda_stream);
+
+/* The resort step (Sec. 2.3: particles re-binned into cells; Sec. 3.3: its
+ * cost under shear) on its own: a stable least-significant-digit radix sort
+ * of n cell keys (host array, each below 2^bits, 1 <= bits <= 32), the same
+ * device code a handle runs at every list build.  order (n, host) receives
+ * the permutation that sorts the keys, equal keys kept in input order;
+ * sorted_keys (n, host, may be NULL) the sorted keys.  Device buffers are
+ * allocated and freed inside the call, which returns after its work (on
+ * cuda_stream, NULL for the default stream) has finished.  1 <= n <= 2^24.
+ * Errors: LE_ERR_INVALID_ARG (sizes, a key of more than `bits` bits),
+ * LE_ERR_OOM, LE_ERR_CUDA. */
+LE_API le_status le_sort_cell_keys(int64_t n, const uint32_t *keys, int bits, uint32_t *order,
+                                   uint32_t *sorted_keys, void *cuda_stream);
 
 LE_API le_status le_destroy(le_sim *s);
 LE_API const char *le_last_error(const le_sim *s);

@@ -27,7 +27,7 @@ LE_OK = 0
 STATUS = {
     0: "LE_OK", 1: "LE_ERR_INVALID_ARG", 2: "LE_ERR_CUDA", 3: "LE_ERR_OOM",
     4: "LE_ERR_BOX_TOO_SMALL", 5: "LE_ERR_BOND_BROKEN", 6: "LE_ERR_NONFINITE",
-    7: "LE_ERR_CAPACITY", 8: "LE_ERR_TIMEOUT", 9: "LE_ERR_STATE",
+    7: "LE_ERR_CAPACITY", 8: "LE_ERR_TIMEOUT", 9: "LE_ERR_STATE", 10: "LE_ERR_RANGE",
 }
 LE_FP64, LE_FP32 = 0, 1
 LE_THERMO_NONE, LE_THERMO_PECULIAR, LE_THERMO_ABSOLUTE, LE_THERMO_DPD = 0, 1, 2, 3
@@ -116,6 +116,9 @@ def lib():
                 "le_forces_noalloc": (C.c_int, [_D, C.c_double, C.c_double, C.c_double,
                                                 C.POINTER(le_params), C.c_int64, C.c_int64,
                                                 _D, _D, _P]),
+                "le_sort_cell_keys": (C.c_int, [C.c_int64, C.POINTER(C.c_uint32), C.c_int,
+                                                C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                                _P]),
                 "le_destroy": (C.c_int, [_P]),
                 "le_last_error": (C.c_char_p, [_P]),
                 "le_status_string": (C.c_char_p, [C.c_int]),
@@ -136,6 +139,7 @@ def exported_symbols() -> list[str]:
             "le_set_launch", "le_tune", "le_batch_tune",
             "le_get_state", "le_set_state", "le_set_eager", "le_destroy", "le_last_error",
             "le_status_string", "le_forces_noalloc", "le_estimate_device_bytes",
+            "le_sort_cell_keys",
             "le_batch_create", "le_batch_add", "le_batch_remove", "le_batch_step",
             "le_batch_destroy", "le_batch_last_error"]
 
@@ -292,6 +296,19 @@ def le_forces_noalloc(box, shear_rate: float, rc: float, skin: float, params: le
                                  out.ctypes.data_as(_D), _stream_handle(stream))
     _check(None, st)
     return out
+
+
+def le_sort_cell_keys(keys, bits: int, stream=None):
+    """(order, sorted keys) of the library's stable radix sort of cell keys."""
+    k = np.ascontiguousarray(keys, dtype=np.uint32)
+    order = np.empty_like(k)
+    out = np.empty_like(k)
+    u32 = C.POINTER(C.c_uint32)
+    st = lib().le_sort_cell_keys(k.size, k.ctypes.data_as(u32), int(bits),
+                                 order.ctypes.data_as(u32), out.ctypes.data_as(u32),
+                                 _stream_handle(stream))
+    _check(None, st)
+    return order, out
 
 
 def le_estimate_device_bytes(box, shear_rate: float, rc: float, skin: float, params: le_params,

@@ -141,6 +141,8 @@ le_status status_from_err(le_sim *s, int err) {
   if (err & kErrCapacity) return fail(s, LE_ERR_CAPACITY, "neighbour list capacity exceeded");
   if (err & kErrSlot) return fail(s, LE_ERR_BOND_BROKEN, "a bond spans more than one cell");
   if (err & kErrTimeout) return fail(s, LE_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up");
+  if (err & kErrRange)
+    return fail(s, LE_ERR_RANGE, "a sampled |vx| above 1000 or m vy^2 above 2000 (profile range)");
   return LE_OK;
 }
 
@@ -470,6 +472,7 @@ LE_API const char *le_status_string(le_status st) {
     case LE_ERR_CAPACITY: return "neighbour list capacity exceeded";
     case LE_ERR_TIMEOUT: return "device wait timed out";
     case LE_ERR_STATE: return "call out of order";
+    case LE_ERR_RANGE: return "sampled value outside the profile range";
   }
   return "unknown status";
 }

@@ -58,7 +58,12 @@ enum ErrBits : int {
   kErrCapacity = 4,   // neighbour list overflow
   kErrSlot = 8,       // a bonded pair outside the 90-slot window
   kErrTimeout = 16,   // a bounded wait on a bulk copy gave up
+  kErrRange = 32,     // a sampled profile value outside its fixed-point range
 };
+// Range of the per-particle profile values held as 2^-20 fixed point in the
+// per-step integer sums: |vx| and m vy^2 beyond these are reported, not summed.
+constexpr float kProfVxMax = 1000.f;
+constexpr float kProfVy2Max = 2000.f;
 
 __host__ __device__ inline int slot_code(int k, int dcy, int dcz, int cross) {
   return (k + 3) | ((dcy + 1) << 3) | ((dcz + 1) << 5) | (cross << 7);

@@ -858,9 +858,14 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   {
     // lanes of a warp mostly share a z bin: one shared atomic per distinct
     // bin and warp (integer sums, so the order of addition does not matter)
-    const float vc = fminf(fmaxf((float)vxw, -1000.f), 1000.f);
+    // a value beyond the fixed-point range is reported as an error (the step
+    // is rolled back), and clamped only so that the integer sums stay defined
+    const float vxf = (float)vxw, vyf = (float)vy2;
+    if (bin >= 0 && !(fabsf(vxf) <= kProfVxMax && vyf <= kProfVy2Max))
+      atomicOr(&d->err, (int)kErrRange);
+    const float vc = fminf(fmaxf(vxf, -kProfVxMax), kProfVxMax);
     const int q = bin >= 0 ? __float2int_rn(vc * (float)kFixP) : 0;
-    const float yc = fminf(fmaxf((float)vy2, 0.f), 2000.f);
+    const float yc = fminf(fmaxf(vyf, 0.f), kProfVy2Max);
     const int qy = bin >= 0 ? __float2int_rn(yc * (float)kFixP) : 0;
     unsigned todo = __ballot_sync(0xffffffffu, bin >= 0);
     while (todo) {

@@ -10,14 +10,17 @@
 // with every buffer carved out of one file-scope static device array.
 //
 // The static array lives on every device that loads this library until the
-// process exits.  Its device address is looked up once per device, with that
-// device current, by the first call made on it; make that first call before
-// any stream capture begins.  Every call shares the array and leaves its
-// contents behind; what must start at zero is cleared by each call.  A call
-// returns only after its device work has finished, and calls from different
-// host threads are serialised by a lock, so within one process calls never
-// overlap on the GPU; work from elsewhere that overlapped a call on the same
-// array would race with it.
+// process exits.  Its device address is looked up, with the device current,
+// by the first call made in each CUDA context (a device's primary context,
+// or a new one after the old one was reset or destroyed: the module, and with
+// it the array, may then sit at another address); make the first call on a
+// device before any stream capture begins.  Every call shares the array and
+// leaves its contents behind; what must start at zero is cleared by each
+// call.  A call returns only after its device work has finished, and calls
+// from different host threads are serialised by a lock, so within one
+// process calls never overlap on the GPU; work from elsewhere that overlapped
+// a call on the same array would race with it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,21 +42,66 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_lock;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
+// the address of the array in the context it was looked up in
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;
+  unsigned char *addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 
-// Device address of the static array for the current device (looked up once).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Identity of the current CUDA context (unique for the life of the process),
+// through the driver entry points, so the library needs no link to libcuda.
+cudaError_t current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000,
+                                                     cudaEnableDefault, &qa);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+    if (e != cudaSuccess) return e;
+    if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    get_id = reinterpret_cast<CtxGetIdFn>(b);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of the static array in the current context, looked up again
+// whenever the context differs from the one of the cached address.
 cudaError_t scratch_address(unsigned char **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e == cudaErrorDeviceUninitialized) {
+    // no context is current yet: the runtime creates the device's primary
+    // context on this first symbol lookup
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = current_context_id(&id);
+  }
+  if (e != cudaSuccess) return e;
+  ScratchAddr &c = g_scratch_addr[dev];
+  if (!c.addr || c.ctx_id != id) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+    c.addr = static_cast<unsigned char *>(p);
+    c.ctx_id = id;
   }
-  *out = g_scratch_addr[dev];
+  *out = c.addr;
   return cudaSuccess;
 }
 

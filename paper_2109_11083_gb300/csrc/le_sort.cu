@@ -308,3 +308,47 @@ void launch_batch_sort(const BatchGrid &bg, cudaStream_t st) {
 }
 
 }  // namespace le
+
+// ---------------------------------------------------------------- C entry
+// The resort step on its own: a stable sort of cell keys, returning the
+// permutation (see le_sort_cell_keys in le.h).
+#include <vector>
+
+#include "../../include/le.h"
+
+extern "C" LE_API le_status le_sort_cell_keys(int64_t n, const uint32_t *keys, int bits,
+                                              uint32_t *order, uint32_t *sorted_keys,
+                                              void *cuda_stream) {
+  using namespace le;
+  if (n < 1 || n > kMaxParticles || !keys || !order || bits < 1 || bits > 32)
+    return LE_ERR_INVALID_ARG;
+  if (bits < 32)
+    for (int64_t i = 0; i < n; ++i)
+      if (keys[i] >> bits) return LE_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int blocks = (int)((n + kSortTile - 1) / kSortTile);
+  const size_t nb = sizeof(uint32_t) * (size_t)n;
+  uint32_t *buf = nullptr;  // key[0], key[1], val[0], val[1], hist, part
+  const size_t hist = (size_t)kSortBuckets * blocks, part = sort_scan_parts(blocks);
+  const size_t words = 4 * (size_t)n + hist + part;
+  if (cudaMalloc(&buf, words * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return LE_ERR_OOM;
+  }
+  uint32_t *key[2] = {buf, buf + n}, *val[2] = {buf + 2 * n, buf + 3 * n};
+  std::vector<uint32_t> iota((size_t)n);
+  for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (uint32_t)i;
+  cudaError_t e = cudaMemcpyAsync(key[0], keys, nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(val[0], iota.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    radix_sort_pairs(key, val, buf + 4 * n, buf + 4 * n + hist, (int)n, bits, blocks, st);
+    e = cudaGetLastError();
+  }
+  const int res = sort_passes_for(bits) & 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(order, val[res], nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && sorted_keys)
+    e = cudaMemcpyAsync(sorted_keys, key[res], nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  return e == cudaSuccess ? LE_OK : LE_ERR_CUDA;
+}

@@ -343,3 +343,28 @@ def test_full_size_box_sampled_forces():
     print(f"full size: FP32 errors (flip-resolved) {FP32_SEEN}")
     assert sim.counters()["rebuilds"] >= 1
     sim.close()
+
+
+def test_profile_value_out_of_range_is_reported_and_rolled_back():
+    """A sampled |vx| above the fixed-point range of the profile sums (1000)
+    is an error with the state rolled back, not a silently clamped sum."""
+    pos = np.array([[2.0, 2.0, 2.0], [6.0, 6.0, 6.0]])
+    vel = np.array([[1500.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    sim = le.Sim(10.0, 0.0, 2.5, 0.3, thermostat=0, dt=0.0001, profile_bins=4)
+    sim.set_particles(pos, vel)
+    r0, v0 = sim.positions()
+    with pytest.raises(le.LEError) as e:
+        sim.step(3)
+    assert e.value.status == 10
+    r1, v1 = sim.positions()
+    assert np.array_equal(r0, r1) and np.array_equal(v0, v1)
+    assert sim.counters()["step"] == 0
+    sim.close()
+    # within range the same system steps and samples normally
+    vel[0, 0] = 900.0
+    sim = le.Sim(10.0, 0.0, 2.5, 0.3, thermostat=0, dt=0.0001, profile_bins=4)
+    sim.set_particles(pos, vel)
+    sim.step(3)
+    vx, cnt = sim.velocity_profile()
+    assert cnt.sum() == 6 and np.nanmax(vx) == pytest.approx(900.0, rel=1e-6)
+    sim.close()
