@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="box workload: skip the bounded batched and served sub-records")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels without CUDA graphs (for profilers that cannot see "
                          "kernels inside conditional graphs)")
@@ -73,17 +75,10 @@ def dist_info():
 
 
 def shard_systems(specs, rank: int, world: int):
-    """The systems of `rank` among `world` ranks: independent boxes need no
-    exchange, so each goes to exactly one rank, largest first to the least
-    loaded rank (deterministic: every rank computes the same assignment)."""
-    order = sorted(range(len(specs)), key=lambda k: (-specs[k]["n"], k))
-    load = [0] * world
-    owner = [0] * len(specs)
-    for k in order:
-        r = min(range(world), key=lambda q: (load[q], q))
-        owner[k] = r
-        load[r] += specs[k]["n"]
-    return [specs[k] for k in range(len(specs)) if owner[k] == rank]
+    """The systems of `rank` among `world` ranks (the package's placement:
+    independent boxes need no exchange, so each goes to exactly one rank)."""
+    from paper_2109_11083_gb300.placement import shard_systems as shard
+    return shard(specs, rank, world)
 
 
 def job_totals(seconds: float, units: float):
@@ -128,6 +123,62 @@ def oracle_rate(n_sample: int, target_s: float, max_steps: int | None = None):
     s.run(steps)
     dt = time.perf_counter() - t0
     return n_sample * steps / dt, steps, dt
+
+
+def _oracle_worker(n_sample: int, target_s: float, barrier, out):
+    """One host core's share of the all-core oracle rate (spawned process)."""
+    import oracle
+    base = synth.lj_box_4m()
+    w = synth.scaled_lj(base, n_sample)
+    pos, vel = synth.lj_initial_state(w)
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * w.box)
+    p = oracle.params(w.box, w.shear_rate, w.rc, dt=w.dt, xi=w.xi, kT=w.kT, seed=w.seed)
+    s = oracle.State(p, pos, vel)
+    t0 = time.perf_counter()
+    s.run(1)
+    steps = max(1, int(target_s / max(time.perf_counter() - t0, 1e-6)))
+    barrier.wait()
+    t0 = time.perf_counter()
+    s.run(steps)
+    out.put((n_sample * steps, time.perf_counter() - t0))
+
+
+def oracle_rate_all_cores(n_sample: int, target_s: float, procs: int):
+    """The oracle, as it stands (one thread per process), run concurrently as
+    `procs` independent processes, one per host core, each on its own copy of
+    an n_sample-particle sub-box: (summed particle-steps/s, seconds)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()      # compiled once, before the processes load it
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(n_sample, target_s, barrier, q))
+          for _ in range(procs)]
+    for pr in ps:
+        pr.start()
+    res = [q.get() for _ in ps]
+    for pr in ps:
+        pr.join()
+    return sum(u / t for u, t in res), max(t for _, t in res)
+
+
+def cpu_baseline_record():
+    """The oracle on the host's cores: one thread, then every core the
+    process may run on (os.sched_getaffinity), each on sub-boxes of the
+    benchmark's LJ workload (the oracle's cost per particle-step does not
+    depend on N: cell list)."""
+    cores = len(os.sched_getaffinity(0))
+    rate1, steps, secs = oracle_rate(131072, 10.0)
+    rate_all, secs_all = oracle_rate_all_cores(32768, 8.0, cores)
+    return {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "host_cores": cores,
+            "sample": (f"{cores} concurrent processes (one per host core), each stepping its "
+                       f"own 32768-particle sub-box of the same LJ workload for ~{secs_all:.0f} s "
+                       f"(FP64 oracle, cell list, one thread each)"),
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"131072-particle sub-box, {steps} oracle steps "
+                                        f"({secs:.1f} s, one thread)"}}
 
 
 def run_reference(args):
@@ -254,6 +305,17 @@ def profiled_traffic(kernel_file: str):
         return None
 
 
+def fp32_error_statement():
+    """The FP32 path's measured error against the FP64 oracle per output, as
+    recorded by the GPU parity tests in the committed summary (None when the
+    summary is absent)."""
+    path = os.path.join(ROOT, "profiles", "fp32_error_lj.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return None
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_info()
@@ -317,10 +379,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            rate, steps, secs = oracle_rate(131072, 12.0)
-            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"131072-particle sub-box of the same LJ workload, {steps} oracle "
-                             f"steps ({secs:.1f} s, FP64, cell list, one thread)"}
+            cpu = cpu_baseline_record()
         e2e = None
         if not args.no_e2e:
             import torch as _t
@@ -342,6 +401,28 @@ def run_ours(args):
                    "d2h_bytes_per_step": (48 * w.n + 8 * 3 + 16 * 20) / args.steps,
                    "what": "le_set_particles (host pinned pos/vel, initial list and forces) + "
                            "le_step(K) + le_positions + le_stress + le_velocity_profile"}
+        sub = {}
+        if not args.no_sub and world == 1:
+            # the metric's other half, bounded: batched and served forms against
+            # the plain one-system-per-launch form on this GPU, equal accuracy
+            # checked bitwise (outside the timed region of the line's value)
+            specs = synth.batched_systems(count=256)
+            rec = measure_batched(le, specs, 64, 3, compare=True, tune_steps=0, n_check=16)
+            sub["batched"] = {"config": batched_config(specs, 1), "steps": 64,
+                              "value": rec["value"], "unit": UNIT, "plain": rec["plain"],
+                              "batched_over_plain": rec["batched_over_plain"],
+                              "equal_accuracy": rec["equal_accuracy"]}
+            from paper_2109_11083_gb300 import serve
+            # the request stream at the configured 50 arrivals/s, and the same
+            # requests arriving 20 times faster (a backlog: the capacity of
+            # each form), each against the plain one-at-a-time server
+            srv = serve.served_record(count=60, steps=400, rate=50.0, n_check=6,
+                                      plain_fifo_too=True)
+            srv["config"] = {"workload": "served_60_requests_poisson50_lj_kg_fp32"}
+            sat = serve.served_record(count=60, steps=400, rate=1000.0, plain_fifo_too=True)
+            sat["config"] = {"workload": "served_60_requests_poisson1000_lj_kg_fp32"}
+            sub["served"] = srv
+            sub["served_backlog"] = sat
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -364,6 +445,10 @@ def run_ours(args):
             "mean_list_length": mean_nb,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
+        line.update(sub)
+        fp32 = fp32_error_statement()
+        if fp32:
+            line["fp32_error"] = fp32
         print(json.dumps(line), flush=True)
     sim.close()
     if world > 1:
@@ -383,33 +468,18 @@ def make_box_sim(le, spec, stream=None):
     return sim
 
 
-def run_batched(args):
-    """256 independent LJ boxes of uneven N (500 to 32,000) stepped one handle at a time
-    (plain) and all together in one batch, equal accuracy checked bitwise."""
+def measure_batched(le, specs, steps: int, warmup: int, compare: bool = True,
+                    tune_steps: int = 32, barrier=lambda: None, world: int = 1,
+                    n_check: int = 16):
+    """Boxes `specs` stepped one handle at a time (plain), as one untuned
+    batch, and as a batch with launch shapes from the autotuner; members
+    checked bitwise against plain.  Returns the timings and checks."""
     import torch
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", rank=rank, world_size=world)
-    torch.cuda.set_device(local)
-    import paper_2109_11083_gb300 as le
-    all_specs = synth.batched_systems(count=args.systems)
-    # N > 1: the boxes are sharded over the ranks (no exchange); the total work
-    # is fixed, so this is strong scaling
-    specs = shard_systems(all_specs, rank, world) if world > 1 else all_specs
-    total = sum(s["n"] for s in specs)
-    total_all = sum(s["n"] for s in all_specs)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-    compare = not args.no_plain
     plain = [make_box_sim(le, s) for s in specs] if compare else []
     batched = [make_box_sim(le, s) for s in specs] if compare else []
     tuned = [make_box_sim(le, s) for s in specs]
-    w = max(args.warmup, 3)
+    total = sum(s["n"] for s in specs)
+    w = max(warmup, 3)
     for s in plain:
         s.step(w)
     b = le.Batch()
@@ -426,29 +496,29 @@ def run_batched(args):
     bt.step(w)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tf, tl, tms = bt.tune(32) if compare else (None, None, None)
+    tf, tl, tms = bt.tune(tune_steps) if (compare and tune_steps) else (None, None, None)
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t0
     barrier()
     t0 = time.perf_counter()
     for s in plain:
-        s.step(args.steps)
+        s.step(steps)
     barrier()
     t_plain = time.perf_counter() - t0
     t0 = time.perf_counter()
     if compare:
-        b.step(args.steps)
+        b.step(steps)
     barrier()
     t_untuned = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bt.step(args.steps)
+    bt.step(steps)
     barrier()
     t_batch = time.perf_counter() - t0
-    t_plain, u_plain = job_totals(t_plain, total * args.steps)
-    t_untuned, u_untuned = job_totals(t_untuned, total * args.steps)
-    t_batch, u_batch = job_totals(t_batch, total * args.steps)
+    t_plain, u_plain = job_totals(t_plain, total * steps)
+    t_untuned, u_untuned = job_totals(t_untuned, total * steps)
+    t_batch, u_batch = job_totals(t_batch, total * steps)
     equal = True
-    for k in range(0, len(plain), max(1, len(plain) // 16)):
+    for k in range(0, len(plain), max(1, len(plain) // n_check)):
         rp, vp = plain[k].positions()
         for other in (batched[k], tuned[k]):
             rb, vb = other.positions()
@@ -457,17 +527,11 @@ def run_batched(args):
         flag = torch.tensor([1 if equal else 0], device="cuda", dtype=torch.int32)
         torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MIN)
         equal = bool(flag.item())
-    value = u_batch / t_batch
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": w, "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"batched_{len(all_specs)}_uneven_lj_fp32",
-                       "systems": len(all_specs), "total_particles": total_all,
-                       "parallelism": f"systems sharded over {world} ranks" if world > 1 else "single",
-                       "n_range": [500, 32000],
-                       "density_range": [0.7, 0.9], "shear_range": [1e-3, 1.0], "rc": 2.5,
-                       "skin": 0.3, "dt": 0.005},
+    b.close()
+    bt.close()
+    for s in plain + batched + tuned:
+        s.close()
+    return {"value": u_batch / t_batch, "unit": UNIT, "t_batch": t_batch, "warmup": w,
             "plain": {"value": u_plain / t_plain, "unit": UNIT,
                       "what": "each box stepped by its own le_step, one after another"}
             if compare else None,
@@ -475,15 +539,51 @@ def run_batched(args):
             "autotune": {"force_threads": tf, "list_threads": tl, "seconds": t_tune,
                          "trial_ms_per_step": tms,
                          "untuned_value": u_untuned / t_untuned} if compare else None,
-            "equal_accuracy": {"bitwise_equal_members": equal, "checked": 16,
+            "equal_accuracy": {"bitwise_equal_members": equal,
+                               "checked": len(range(0, len(plain), max(1, len(plain) // n_check))),
                                "what": "plain vs batched and vs autotuned batched"}
             if compare else None}
+
+
+def batched_config(all_specs, world):
+    return {"workload": f"batched_{len(all_specs)}_uneven_lj_fp32",
+            "systems": len(all_specs), "total_particles": sum(s["n"] for s in all_specs),
+            "parallelism": f"systems sharded over {world} ranks" if world > 1 else "single",
+            "n_range": [500, 32000], "density_range": [0.7, 0.9], "shear_range": [1e-3, 1.0],
+            "rc": 2.5, "skin": 0.3, "dt": 0.005}
+
+
+def run_batched(args):
+    """256 independent LJ boxes of uneven N (500 to 32,000) stepped one handle at a time
+    (plain) and all together in one batch, equal accuracy checked bitwise."""
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    import paper_2109_11083_gb300 as le
+    all_specs = synth.batched_systems(count=args.systems)
+    # N > 1: the boxes are sharded over the ranks (no exchange); the total work
+    # is fixed, so this is strong scaling
+    specs = shard_systems(all_specs, rank, world) if world > 1 else all_specs
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+    rec = measure_batched(le, specs, args.steps, args.warmup, compare=not args.no_plain,
+                          barrier=barrier, world=world)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": rec["warmup"],
+            "ms_per_step": rec["t_batch"] / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": batched_config(all_specs, world),
+            "plain": rec["plain"], "batched_over_plain": rec["batched_over_plain"],
+            "autotune": rec["autotune"], "equal_accuracy": rec["equal_accuracy"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    b.close()
-    bt.close()
-    for s in plain + batched + tuned:
-        s.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -28,7 +28,7 @@ using namespace le;
 namespace {
 constexpr int kChunk = 16;
 constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
-constexpr int kStateVersion = 3;
+constexpr int kStateVersion = 4;
 }  // namespace
 
 struct le_sim {
@@ -160,18 +160,20 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
     void *p, *plo, *v, *ft, *fc;
     float4 *pb;
     int *gid;
+    int4 *q = nullptr;
     CKS(dalloc(s, (char **)&p, n * vb));
     plo = nullptr;
     if (prec == 1) CKS(dalloc(s, (char **)&plo, n * sizeof(float4)));
+    if (prec == 1) CKS(dalloc(s, &q, n));
     CKS(dalloc(s, (char **)&v, n * vb));
     CKS(dalloc(s, (char **)&ft, n * vb));
     CKS(dalloc(s, (char **)&fc, n * vb));
     CKS(dalloc(s, &pb, n));
     CKS(dalloc(s, &gid, n));
     if (prec == 1) {
-      s->s.f32[k] = Bufs<float>{(float4 *)p, (float4 *)plo, (float4 *)v, (float4 *)ft, (float4 *)fc, pb, gid};
+      s->s.f32[k] = Bufs<float>{(float4 *)p, (float4 *)plo, (float4 *)v, (float4 *)ft, (float4 *)fc, pb, gid, q};
     } else {
-      s->s.f64[k] = Bufs<double>{(D4 *)p, (float4 *)plo, (D4 *)v, (D4 *)ft, (D4 *)fc, pb, gid};
+      s->s.f64[k] = Bufs<double>{(D4 *)p, (float4 *)plo, (D4 *)v, (D4 *)ft, (D4 *)fc, pb, gid, nullptr};
     }
   }
   Work &w = s->s.w;
@@ -225,6 +227,7 @@ void choose_cells(le_sim *s) {
   while ((1ll << bits) < (long long)g.ncell) ++bits;
   g.sort_bits = bits;
   s->s.sort_passes = sort_passes_for(bits);
+  set_fixed_point(g);
 }
 
 // Per-system parameters and per-precision kernel constants.

@@ -15,6 +15,14 @@
 //   the same unwrapped coordinate, which is the wrapped peculiar velocity
 //   exactly (both v and v_s shift by shear_rate*Lz across the face).
 //
+//   In FP32 mode the pair loop reads a second, derived copy of p: q, the
+//   displacement in int32 fixed point of 2^-S (S = Geom::qshift, 27 for the
+//   usual cells), rounded from the double-float p = hi + lo.  A pair's
+//   separation in those units, q_i - q_j + off(slot) with integer cell
+//   edges and cross-face shift, is exact integer arithmetic; its one rounding
+//   is the conversion to float.  FP32 storage of p itself (24 bits) would
+//   round every position and every difference.
+//
 //   A neighbour-list entry is (j | slot << 24): slot names the image of j as
 //   seen from i's build cell, as bit fields: an x-cell offset k in [-3,4]
 //   (3 bits), y and z cell offsets in [-1,1] (2 bits each) and whether the
@@ -126,6 +134,12 @@ struct Geom {
   float inv_lc[3];                // 1 / cell edge
   float half_lc_f[3];             // half cell edge with a rounding margin (list pruning)
   float lc_hi[3], lc_lo[3];       // cell edge as an unevaluated float sum
+  // FP32 fixed-point positions q (units of 2^-qshift): cell edges in those
+  // units and the largest |p| component the units can hold with the pair
+  // separations (beyond it the step reports LE_ERR_RANGE)
+  int qshift;
+  int qL[3];
+  float qmax;
   KConst<float> cf;
   KConst<double> cd;
 };
@@ -142,7 +156,8 @@ struct Dyn {
   double dX_build;       // dX(build_step)
   double f_build;        // dX(build_step) - m_build * lx, in [0, lx)
   double s;              // continuous cross-face shift of this step
-  float s_f;             // s rounded to float (FP32 pair kernel)
+  float s_f;             // s rounded to float
+  int s_q;               // s in FP32 fixed-point position units (2^-qshift)
   float f_hi, f_lo;      // f_build as an unevaluated float sum (FP32 re-basing)
   int m_build;
   int win_lo[2], win_hi[2];  // x-cell window of rows across the top/bottom face, [dcz=-1, dcz=+1]
@@ -179,6 +194,7 @@ template <class R> struct Bufs {
   typename Vec<R>::T *fc;  // conservative force (LJ + FENE)
   float4 *pb;              // p at the last build (x,y,z); w = build cell id (int bits)
   int *gid;                // caller's particle id
+  int4 *q;                 // FP32 mode: p in fixed point (x,y,z); w = bits of p.w (float)
 };
 
 // Shared (not double-buffered) work arrays of one system.
@@ -210,6 +226,7 @@ __device__ __forceinline__ Bufs<R> pick(int cur, const Bufs<R> &a, const Bufs<R>
   r.fc = cur ? b.fc : a.fc;
   r.pb = cur ? b.pb : a.pb;
   r.gid = cur ? b.gid : a.gid;
+  r.q = cur ? b.q : a.q;
   return r;
 }
 

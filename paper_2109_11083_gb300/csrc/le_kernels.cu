@@ -46,6 +46,19 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float a) {
   lo = __fsub_rn(lo, __fsub_rn(hi, s));
 }
 
+// FP32 fixed-point copy of a displacement hi + lo: each part scaled by 2^S
+// (exact) and rounded to an integer, so the copy is p rounded to 2^-S within
+// one unit; w carries the bits of hi.w (the build cell's reference z).
+__device__ __forceinline__ int4 quantize(const Geom &g, const float4 &hi, const float4 &lo) {
+  const float sc = __int_as_float((127 + g.qshift) << 23);  // 2^S
+  int4 q;
+  q.x = __float2int_rn(hi.x * sc) + __float2int_rn(lo.x * sc);
+  q.y = __float2int_rn(hi.y * sc) + __float2int_rn(lo.y * sc);
+  q.z = __float2int_rn(hi.z * sc) + __float2int_rn(lo.z * sc);
+  q.w = __float_as_int(hi.w);
+  return q;
+}
+
 __device__ __forceinline__ void cell_coords(const Geom &g, int c, int &cx, int &cy, int &cz) {
   cx = c % g.nc[0];
   int r = c / g.nc[0];
@@ -152,6 +165,10 @@ __device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bu
       two_sum_acc(p.y, lo.y, dt * v.y);
       two_sum_acc(p.z, lo.z, dt * v.z);
       b.plo[i] = lo;
+      // a displacement beyond the fixed-point range is reported (LE_ERR_RANGE)
+      if (!(fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))) < g.qmax))
+        atomicOr(&d->err, (int)kErrRange);
+      b.q[i] = quantize(g, p, lo);
     } else {
       p.x += dt * v.x;
       p.y += dt * v.y;
@@ -280,6 +297,7 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
     }
     d->s = s;
     d->s_f = (float)s;
+    d->s_q = (int)llrint(ldexp(s, g.qshift));
     d->dX = dX1;
     d->step = n1;
     d->rebuild = need ? 1 : 0;
@@ -500,6 +518,68 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   vir += tx * dz;
 }
 
+// FP32 separations from the fixed-point copies q (units 2^-S): for a list
+// entry e of particle o, d' = 2^S (p_o - p_j + off(slot)) =
+//   q_o - q_j + (k lx, dcy ly, dcz lz) + cross dcz s   (all in units),
+// exact in wrapping 32-bit integer arithmetic (|d'| < 2^31 for every list
+// entry), then rounded once to float.  The slot fields' biases (k + 3,
+// dcy + 1, dcz + 1) are folded into per-particle constants.
+struct SlotQ {
+  uint32_t X0, Y0, Z0;       // q_o minus (3 lx, ly, lz) in units
+  uint32_t LX, LY, LZ, Sq;   // cell edges and the cross-face shift s(t) in units
+  float inv;                 // 2^-S
+};
+__device__ __forceinline__ SlotQ slot_q(const Geom &g, int s_q, const int4 &qo) {
+  SlotQ G;
+  G.LX = (uint32_t)g.qL[0];
+  G.LY = (uint32_t)g.qL[1];
+  G.LZ = (uint32_t)g.qL[2];
+  G.Sq = (uint32_t)s_q;
+  G.X0 = (uint32_t)qo.x - 3u * G.LX;
+  G.Y0 = (uint32_t)qo.y - G.LY;
+  G.Z0 = (uint32_t)qo.z - G.LZ;
+  G.inv = __int_as_float((127 - g.qshift) << 23);
+  return G;
+}
+// d' (float, units of 2^-S) of entry e against the neighbour's copy qj
+__device__ __forceinline__ void q_sep(uint32_t e, const SlotQ &G, const int4 &qj, float &dx,
+                                      float &dy, float &dz) {
+  const uint32_t k = e & 7u, dy1 = (e >> 3) & 3u, dz1 = (e >> 5) & 3u;
+  const uint32_t cross = 0u - ((e >> 7) & 1u);          // all ones across the face
+  const uint32_t czs = (dz1 * G.Sq - G.Sq) & cross;      // cross dcz s
+  dx = __int2float_rn((int)(k * G.LX + G.X0 - (uint32_t)qj.x + czs));
+  dy = __int2float_rn((int)(dy1 * G.LY + G.Y0 - (uint32_t)qj.y));
+  dz = __int2float_rn((int)(dz1 * G.LZ + G.Z0 - (uint32_t)qj.z));
+}
+// the same separation in length units (the scaling by 2^-S is exact)
+__device__ __forceinline__ void q_sep_real(uint32_t e, const SlotQ &G, const int4 &qj, float &dx,
+                                           float &dy, float &dz) {
+  q_sep(e, G, qj, dx, dy, dz);
+  dx = __fmul_rn(dx, G.inv);
+  dy = __fmul_rn(dy, G.inv);
+  dz = __fmul_rn(dz, G.inv);
+}
+
+// FP32 LJ pair from d' = 2^S d: a = 1/r'^2, ir2 = 2^2S a (exact scaling),
+// the force factor ir2 ir6 (c12 ir6 - c6); the force and the virial are
+// accumulated in units of 2^S and 2^2S (rescaled after the list loop).
+__device__ __forceinline__ void lj_pair_q(const SlotQ &G, const int4 &qj, uint32_t e, float rc2q,
+                                          float s2S, float c12, float c6, float &fx, float &fy,
+                                          float &fz, float &vir) {
+  float dx, dy, dz;
+  q_sep(e, G, qj, dx, dy, dz);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  // branch-free, as in the FP64 path; r2 > 0 for every list entry
+  const float ir2 = recip<float>(r2) * s2S;
+  const float ir6 = ir2 * ir2 * ir2;
+  const float fr = r2 < rc2q ? ir2 * ir6 * fmaf(c12, ir6, -c6) : 0.f;
+  const float tx = fr * dx;
+  fx += tx;
+  fy += fr * dy;
+  fz += fr * dz;
+  vir += tx * dz;
+}
+
 // DPD (Eqs. 6-8, read as the fluctuation-dissipation form): the dissipative
 // and random pair forces for r < rc, added to t (the thermostat part of the
 // total force, not the conservative force).  v_ij is taken against the image
@@ -522,11 +602,16 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 template <class R>
 __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V4<R> &vi, int gi,
                                          const Bufs<R> &b, uint32_t e, const SlotGeo<R> &G,
-                                         long long n1, R rc2, R &tx, R &ty, R &tz) {
+                                         const SlotQ &GQ, long long n1, R rc2, R &tx, R &ty,
+                                         R &tz) {
   const int j = entry_index(e);
-  const V4<R> pj = load4(b.p + j);
   R dx, dy, dz;
-  slot_sep<R>(e, G, pi, pj, dx, dy, dz);
+  if constexpr (sizeof(R) == 4) {
+    q_sep_real(e, GQ, __ldg(b.q + j), dx, dy, dz);
+  } else {
+    const V4<R> pj = load4(b.p + j);
+    slot_sep<R>(e, G, pi, pj, dx, dy, dz);
+  }
   const R r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
   if (!(r2 < rc2)) return;
   const KConst<R> &K = kc<R>(g);
@@ -632,7 +717,20 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
   R tdx = R(0), tdy = R(0), tdz = R(0);  // DPD pair forces
   V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
-  if (active) pi = b.p[i];
+  // FP32: the fixed-point copy (pair separations) and p rebuilt from it
+  int4 qi = make_int4(0, 0, 0, 0);
+  SlotQ GQ{};
+  if constexpr (sizeof(R) == 4) {
+    if (active) qi = b.q[i];
+    GQ = slot_q(g, d->s_q, qi);
+    pi = make4<R>(__int2float_rn(qi.x) * GQ.inv, __int2float_rn(qi.y) * GQ.inv,
+                  __int2float_rn(qi.z) * GQ.inv, __int_as_float(qi.w));
+  } else {
+    if (active) pi = b.p[i];
+  }
+  // FP32 LJ constants for separations in units of 2^-S
+  const float s2S = __int_as_float((127 + 2 * g.qshift) << 23);   // 2^2S
+  const float rc2q = (float)K.rc2 * s2S;
   V4<R> vi = make4<R>(R(0), R(0), R(0), R(0));
   int gi = 0;
   if (DPD && active) {
@@ -655,27 +753,51 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
     // pairs are still summed in list order (same result for any group size)
     // (FP64 and DPD keep four: their larger register state would spill)
     constexpr int U = (sizeof(R) == 4 && !DPD) ? kForceUnroll : 4;
-    for (; r + U <= rn; r += U) {
-      uint32_t e[U];
-      V4<R> q[U];
+    if constexpr (sizeof(R) == 4) {
+      for (; r + U <= rn; r += U) {
+        uint32_t e[U];
+        int4 q[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) e[u] = rows[r + u][lane];
+        for (int u = 0; u < U; ++u) e[u] = rows[r + u][lane];
 #pragma unroll
-      for (int u = 0; u < U; ++u) q[u] = load4(b.p + entry_index(e[u]));
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        lj_pair<R>(pi, q[u], e[u], G, rc2, c12, c6, fx, fy, fz, vir);
-      if constexpr (DPD) {
+        for (int u = 0; u < U; ++u) q[u] = __ldg(b.q + entry_index(e[u]));
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          dpd_pair<R>(g, pi, vi, gi, b, e[u], G, n1, rc2, tdx, tdy, tdz);
+          lj_pair_q(GQ, q[u], e[u], rc2q, s2S, c12, c6, fx, fy, fz, vir);
+        if constexpr (DPD) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            dpd_pair<R>(g, pi, vi, gi, b, e[u], G, GQ, n1, rc2, tdx, tdy, tdz);
+        }
       }
-    }
-    for (; r < rn; ++r) {
-      const uint32_t e = rows[r][lane];
-      const V4<R> q = load4(b.p + entry_index(e));
-      lj_pair<R>(pi, q, e, G, rc2, c12, c6, fx, fy, fz, vir);
-      if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, n1, rc2, tdx, tdy, tdz);
+      for (; r < rn; ++r) {
+        const uint32_t e = rows[r][lane];
+        lj_pair_q(GQ, __ldg(b.q + entry_index(e)), e, rc2q, s2S, c12, c6, fx, fy, fz, vir);
+        if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, GQ, n1, rc2, tdx, tdy, tdz);
+      }
+    } else {
+      for (; r + U <= rn; r += U) {
+        uint32_t e[U];
+        V4<R> q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) e[u] = rows[r + u][lane];
+#pragma unroll
+        for (int u = 0; u < U; ++u) q[u] = load4(b.p + entry_index(e[u]));
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          lj_pair<R>(pi, q[u], e[u], G, rc2, c12, c6, fx, fy, fz, vir);
+        if constexpr (DPD) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            dpd_pair<R>(g, pi, vi, gi, b, e[u], G, GQ, n1, rc2, tdx, tdy, tdz);
+        }
+      }
+      for (; r < rn; ++r) {
+        const uint32_t e = rows[r][lane];
+        const V4<R> q = load4(b.p + entry_index(e));
+        lj_pair<R>(pi, q, e, G, rc2, c12, c6, fx, fy, fz, vir);
+        if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, GQ, n1, rc2, tdx, tdy, tdz);
+      }
     }
     __syncwarp();
     if (lane == 0 && c + 2 < nchunks) {
@@ -690,6 +812,28 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       mbar_wait(&s_bar[warp][c & 1], (uint32_t)(c >> 1) & 1u);
   }
 
+  if constexpr (sizeof(R) == 4) {
+    // the pair sums were taken in units of 2^S (force) and 2^2S (virial)
+    fx *= GQ.inv;
+    fy *= GQ.inv;
+    fz *= GQ.inv;
+    vir *= GQ.inv * GQ.inv;
+  }
+  // separation of o (at po; fixed-point copy qo) from the image of the
+  // particle that bond entry e names, in length units
+  auto bond_sep = [&](const V4<R> &po, const int4 &qo, uint32_t e, R &dx, R &dy, R &dz) {
+    const int j = entry_index(e);
+    if constexpr (sizeof(R) == 4) {
+      q_sep_real(e, slot_q(g, d->s_q, qo), __ldg(b.q + j), dx, dy, dz);
+    } else {
+      const V4<R> pj = load4(b.p + j);
+      R ox, oy, oz;
+      slot_offset<R>(e, G, ox, oy, oz);
+      dx = (po.x - pj.x) + ox;
+      dy = (po.y - pj.y) + oy;
+      dz = (po.z - pj.z) + oz;
+    }
+  };
   R sxz = R(0), ke = R(0);
   int bin = -1;
   R vxw = R(0), vy2 = R(0);
@@ -699,13 +843,8 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       for (int q = 0; q < g.maxb; ++q) {
         const uint32_t e = w.bond_e[(size_t)i * g.maxb + q];
         if (e == kNoBond) break;
-        const int j = entry_index(e);
-        const V4<R> pj = load4(b.p + j);
-        R ox, oy, oz;
-        slot_offset<R>(e, G, ox, oy, oz);
-        const R dx = (pi.x - pj.x) + ox;
-        const R dy = (pi.y - pj.y) + oy;
-        const R dz = (pi.z - pj.z) + oz;
+        R dx, dy, dz;
+        bond_sep(pi, qi, e, dx, dy, dz);
         const R x = R(1) - (dx * dx + dy * dy + dz * dz) / R02;
         if (!(x > R(0))) {
           atomicOr(&d->err, (int)kErrBond);
@@ -726,14 +865,6 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
         // for its bonds), so angles across the sheared face need no extra
         // image arithmetic.
         const R ka = K.ang_k;
-        auto sep = [&](const V4<R> &po, uint32_t e, R &ax, R &ay, R &az) {
-          const V4<R> pq = load4(b.p + entry_index(e));
-          R ox, oy, oz;
-          slot_offset<R>(e, G, ox, oy, oz);
-          ax = (po.x - pq.x) + ox;
-          ay = (po.y - pq.y) + oy;
-          az = (po.z - pq.z) + oz;
-        };
         // force on the end bead at a = r_end - r_mid, the other end at c
         auto end_force = [&](R ax, R ay, R az, R cx, R cy, R cz, R &gx, R &gy, R &gz) {
           const R ia = R(1) / sqrt(ax * ax + ay * ay + az * az);
@@ -753,12 +884,12 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
           const uint32_t eu = w.bond_e[(size_t)i * g.maxb + u];
           if (eu == kNoBond) break;
           R ux, uy, uz;  // r_i - r_j for the bonded neighbour j
-          sep(pi, eu, ux, uy, uz);
+          bond_sep(pi, qi, eu, ux, uy, uz);
           for (int v = u + 1; v < g.maxb; ++v) {
             const uint32_t ev = w.bond_e[(size_t)i * g.maxb + v];
             if (ev == kNoBond) break;
             R vx, vy, vz;
-            sep(pi, ev, vx, vy, vz);
+            bond_sep(pi, qi, ev, vx, vy, vz);
             // i in the middle: the ends sit at -u and -v from i
             R ax, ay, az, cx, cy, cz;
             end_force(-ux, -uy, -uz, -vx, -vy, -vz, ax, ay, az);
@@ -769,13 +900,16 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
           }
           // i at an end: the angles in the middle of j, with j's other bonds
           const int j = entry_index(eu);
-          const V4<R> pj = load4(b.p + j);
+          V4<R> pj = make4<R>(R(0), R(0), R(0), R(0));
+          int4 qj = make_int4(0, 0, 0, 0);
+          if constexpr (sizeof(R) == 4) qj = __ldg(b.q + j);
+          else pj = load4(b.p + j);
           for (int q = 0; q < g.maxb; ++q) {
             const uint32_t ek = w.bond_e[(size_t)j * g.maxb + q];
             if (ek == kNoBond) break;
             if (entry_index(ek) == i) continue;  // the bond back to i
             R kx, ky, kz;  // r_j - r_k
-            sep(pj, ek, kx, ky, kz);
+            bond_sep(pj, qj, ek, kx, ky, kz);
             R ax, ay, az;
             end_force(ux, uy, uz, -kx, -ky, -kz, ax, ay, az);
             fx += ax;
@@ -1080,7 +1214,11 @@ __device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ 
   const V4<R> h = reinterpret_cast<const V4<R> *>(w.tmp_p)[o];
   const R zref = (R(cz) + R(0.5)) * R(g.lc[2]);
   dst.p[k] = make4<R>(h.x, h.y, h.z, zref);
-  if constexpr (sizeof(R) == 4) dst.plo[k] = w.tmp_lo[o];
+  if constexpr (sizeof(R) == 4) {
+    const float4 lo = w.tmp_lo[o];
+    dst.plo[k] = lo;
+    dst.q[k] = quantize(g, make4<float>(h.x, h.y, h.z, zref), lo);
+  }
   dst.pb[k] = make_float4((float)h.x, (float)h.y, (float)h.z, __int_as_float(c));
   dst.v[k] = src.v[o];
   const int gid = src.gid[o];
@@ -1145,6 +1283,8 @@ __global__ void k_relist_prep(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s
   w.Xs[3 * (size_t)k + 1] = ((double)cy + 0.5) * g.lc[1] + (double)q.y;
   w.Xs[3 * (size_t)k + 2] = ((double)cz + 0.5) * g.lc[2] + (double)q.z;
   w.rank[b.gid[k]] = k;
+  // the fixed-point copy of a restored state
+  if constexpr (sizeof(R) == 4) b.q[k] = quantize(g, b.p[k], b.plo[k]);
 }
 
 // Slot-offset tables from d->s (this step) and d->f_build (last build).

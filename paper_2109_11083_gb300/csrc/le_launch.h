@@ -2,6 +2,9 @@
 // le_sort.cu) and the device-side description of one system.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
+
 #include "le_common.cuh"
 
 namespace le {
@@ -35,6 +38,25 @@ struct SysDev {
 };
 
 inline int blocks_for(int n, int threads) { return (n + threads - 1) / threads; }
+
+// FP32 fixed-point position units of a system with cells lc[] already chosen:
+// 2^-S with S the largest shift (at most 27) whose int32 range holds every
+// displacement from a build-cell centre that the rebuild trigger allows --
+// half a cell, the peculiar drift (skin / 2) and the streaming along x of
+// a particle at the top or bottom face until the trigger's shear term fires
+// (|shear| tau rc < skin, so at most skin Lz / (2 rc)) -- and every list
+// separation (< rc + 2 skin), with a factor 2 to spare.
+inline void set_fixed_point(Geom &g) {
+  double lmax = std::max(g.lc[0], std::max(g.lc[1], g.lc[2]));
+  double pmax = 0.5 * lmax + g.skin + (g.shear_rate != 0.0 ? g.skin * g.L[2] / (2.0 * g.rc) : 0.0);
+  pmax = std::max(pmax, g.rl + 2.0 * g.skin);
+  pmax = std::max(pmax, g.fene_R0 + g.skin);
+  int S = 27;
+  while (S > 8 && 2.0 * pmax * std::ldexp(1.0, S) >= 2147483647.0) --S;
+  g.qshift = S;
+  for (int a = 0; a < 3; ++a) g.qL[a] = (int)std::llrint(std::ldexp(g.lc[a], S));
+  g.qmax = (float)(2147483647.0 / 2.0 * std::ldexp(1.0, -S));
+}
 
 void launch_drift(const SysDev &s, cudaStream_t st);
 // use_cond: set the graph's conditional handle h (0 when launched outside a graph)

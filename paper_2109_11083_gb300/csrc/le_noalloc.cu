@@ -207,6 +207,7 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   int bits = 1;
   while ((1ll << bits) < (long long)g.ncell) ++bits;
   g.sort_bits = bits;
+  set_fixed_point(g);
   g.n = (int)n;
   g.npad = (int)((n + 31) / 32 * 32);
   g.maxb = 0;
@@ -224,6 +225,7 @@ template <class R> void carve_set(Carver &cv, Bufs<R> &b, int64_t n, bool lo) {
   b.fc = cv.take<typename Vec<R>::T>(n);
   b.pb = cv.take<float4>(n);
   b.gid = cv.take<int>(n);
+  b.q = lo ? cv.take<int4>(n) : nullptr;
 }
 
 // Lays every buffer of a one-shot force evaluation out in the static array.
@@ -311,6 +313,7 @@ extern "C" LE_API le_status le_forces_noalloc(const double box[3], double shear_
     d.f_build = f;
     d.s = f;
     d.s_f = (float)f;
+    d.s_q = (int)std::llrint(std::ldexp(f, s.g.qshift));
     d.cur = 0;
     cudaError_t e = cudaMemcpyAsync(s.dyn, &d, sizeof d, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.w.acc_prof, 0, 3 * sizeof(long long), st);

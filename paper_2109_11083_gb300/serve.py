@@ -238,33 +238,101 @@ def trace_requests(count: int, steps: int, rate: float = 50.0, max_particles: in
     return out
 
 
+def plain_fifo(requests: list[Request], time_scale: float = 1.0, clock=time.perf_counter):
+    """The plain form of the same stream: one request at a time on its own
+    handle, first come first served.  Returns (latencies, particle-steps,
+    elapsed seconds)."""
+    order = sorted(requests, key=lambda r: r.arrival)
+    lat = []
+    work = 0
+    t0 = clock()
+    for r in order:
+        now = clock() - t0
+        if r.arrival * time_scale > now:
+            time.sleep(r.arrival * time_scale - now)
+        run_alone(r)
+        lat.append(clock() - t0 - r.arrival * time_scale)
+        work += r.n * r.steps
+    return np.array(lat), work, clock() - t0
+
+
+def served_record(count: int, steps: int, rate: float = 50.0, n_check: int = 0,
+                  budget_bytes: int = 150 * 2 ** 30, quantum: int = 100,
+                  plain_fifo_too: bool = False) -> dict:
+    """Serves `count` requests of the trace (each `steps` steps, arrivals at
+    `rate` per second) and summarises latency and throughput.  With n_check >
+    0, the first n_check requests are also run alone, one after another (the
+    plain one-request-per-handle form): their aggregate rate is the plain
+    figure, and each served result must equal its alone result bitwise.  With
+    plain_fifo_too, the whole stream is also served the plain way (one
+    request at a time, first come first served) for its throughput and
+    latency."""
+    reqs = trace_requests(count, steps)
+    srv = Server(budget_bytes=budget_bytes, quantum=quantum)
+    res = srv.run(reqs, time_scale=50.0 / rate)
+    srv.close()
+    lat = np.array([r.latency for r in res])
+    wait = np.array([r.wait for r in res])
+    out = {"value": srv.particle_steps / srv.elapsed, "unit": "particle-steps/s",
+           "requests": count, "steps_per_request": steps, "arrival_rate_per_s": rate,
+           "particles_per_request": [int(min(r.n for r in reqs)), int(max(r.n for r in reqs))],
+           "budget_bytes": budget_bytes, "quantum_steps": quantum,
+           "latency_s": {"p50": float(np.percentile(lat, 50)),
+                         "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean())},
+           "wait_s": {"p50": float(np.percentile(wait, 50)),
+                      "p99": float(np.percentile(wait, 99))},
+           "max_queue": srv.max_queue, "makespan_s": srv.elapsed,
+           "offered_particle_steps_per_s": float(sum(r.n * r.steps for r in reqs) /
+                                                 (max(r.arrival for r in reqs) * 50.0 / rate))}
+    if plain_fifo_too:
+        plat, work, el = plain_fifo(reqs, time_scale=50.0 / rate)
+        out["plain_fifo"] = {"value": work / el, "unit": "particle-steps/s",
+                             "latency_s": {"p50": float(np.percentile(plat, 50)),
+                                           "p99": float(np.percentile(plat, 99))},
+                             "makespan_s": el,
+                             "what": "the same stream served one request at a time, each on "
+                                     "its own handle, first come first served"}
+        out["served_over_plain_fifo"] = out["value"] / (work / el)
+    if n_check > 0:
+        by_id = {r.id: r for r in res}
+        chk = sorted(reqs, key=lambda r: r.id)[:n_check]
+        equal = True
+        t = 0.0
+        for r in chk:
+            t0 = time.perf_counter()
+            eta, prof, cnt = run_alone(r)
+            t += time.perf_counter() - t0
+            got = by_id[r.id]
+            equal = equal and (np.array_equal(prof, got.profile, equal_nan=True)
+                               and np.array_equal(cnt, got.counts)
+                               and (eta == got.viscosity or (eta != eta and got.viscosity
+                                                            != got.viscosity)))
+        plain = sum(r.n * r.steps for r in chk) / t
+        out["plain"] = {"value": plain, "unit": "particle-steps/s",
+                        "what": f"the first {n_check} requests run alone, one after another "
+                                "(handle set-up included, as in the served run)"}
+        out["served_over_plain"] = out["value"] / plain
+        out["equal_accuracy"] = {"bitwise_equal_requests": bool(equal), "checked": n_check}
+    return out
+
+
 def main_bench(args) -> int:
     """`bench.py --workload served`: a Poisson stream of mixed LJ/KG shear-sweep
     requests served with continuous batching; p50/p99 latency and aggregate
     particle-steps/s."""
     count = 200
     steps = max(args.steps // 4, 50)
-    reqs = trace_requests(count, steps)
     rate = float(getattr(args, "arrival_rate", 50.0))
-    srv = Server(budget_bytes=150 * 2 ** 30, quantum=100)
-    res = srv.run(reqs, time_scale=50.0 / rate)
-    srv.close()
-    lat = np.array([r.latency for r in res])
-    wait = np.array([r.wait for r in res])
-    value = srv.particle_steps / srv.elapsed
-    line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+    rec = served_record(count, steps, rate)
+    line = {"metric": "particle-steps/s", "value": rec["value"], "unit": "particle-steps/s",
             "n_gpus": 1, "steps": steps, "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"served_{count}_requests_poisson{rate:g}_lj_kg_fp32",
                        "requests": count, "steps_per_request": steps, "arrival_rate_per_s": rate,
-                       "particles_per_request": [int(min(r.n for r in reqs)),
-                                                 int(max(r.n for r in reqs))],
-                       "budget_bytes": 150 * 2 ** 30, "quantum_steps": 100},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "mean": float(lat.mean())},
-            "wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
-            "max_queue": srv.max_queue, "makespan_s": srv.elapsed,
-            "offered_particle_steps_per_s": float(sum(r.n * r.steps for r in reqs) /
-                                                  (max(r.arrival for r in reqs) * 50.0 / rate))}
+                       "particles_per_request": rec["particles_per_request"],
+                       "budget_bytes": rec["budget_bytes"], "quantum_steps": rec["quantum_steps"]},
+            "latency_s": rec["latency_s"], "wait_s": rec["wait_s"],
+            "max_queue": rec["max_queue"], "makespan_s": rec["makespan_s"],
+            "offered_particle_steps_per_s": rec["offered_particle_steps_per_s"]}
     print(json.dumps(line), flush=True)
     return 0
