@@ -560,24 +560,29 @@ __device__ __forceinline__ void q_sep_real(uint32_t e, const SlotQ &G, const int
   dz = __fmul_rn(dz, G.inv);
 }
 
-// FP32 LJ pair from d' = 2^S d: a = 1/r'^2, ir2 = 2^2S a (exact scaling),
-// the force factor ir2 ir6 (c12 ir6 - c6); the force and the virial are
-// accumulated in units of 2^S and 2^2S (rescaled after the list loop).
-__device__ __forceinline__ void lj_pair_q(const SlotQ &G, const int4 &qj, uint32_t e, float rc2q,
-                                          float s2S, float c12, float c6, float &fx, float &fy,
-                                          float &fz, float &vir) {
-  float dx, dy, dz;
-  q_sep(e, G, qj, dx, dy, dz);
-  const float r2 = dx * dx + dy * dy + dz * dz;
-  // branch-free, as in the FP64 path; r2 > 0 for every list entry
-  const float ir2 = recip<float>(r2) * s2S;
-  const float ir6 = ir2 * ir2 * ir2;
-  const float fr = r2 < rc2q ? ir2 * ir6 * fmaf(c12, ir6, -c6) : 0.f;
-  const float tx = fr * dx;
-  fx += tx;
-  fy += fr * dy;
-  fz += fr * dz;
-  vir += tx * dz;
+// Two FP32 LJ pairs at once with the paired FP32 instructions of this
+// architecture (fma/mul/add.rn.f32x2): lane x of every float2 is pair a,
+// lane y pair b; the sums of the two lanes are kept apart and added once
+// after the list loop.  cut.y = 0 drops pair b (an odd pair left over).
+__device__ __forceinline__ void lj_pair2_q(const SlotQ &G, const int4 &qa, const int4 &qb,
+                                           uint32_t ea, uint32_t eb, float2 cut, float2 s2S,
+                                           float2 c12, float2 mc6, float2 &fx, float2 &fy,
+                                           float2 &fz, float2 &vir) {
+  float ax, ay, az, bx, by, bz;
+  q_sep(ea, G, qa, ax, ay, az);
+  q_sep(eb, G, qb, bx, by, bz);
+  const float2 dx = make_float2(ax, bx), dy = make_float2(ay, by), dz = make_float2(az, bz);
+  const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  const float2 ir2 = __fmul2_rn(make_float2(recip<float>(r2.x), recip<float>(r2.y)), s2S);
+  const float2 ir6 = __fmul2_rn(__fmul2_rn(ir2, ir2), ir2);
+  float2 fr = __fmul2_rn(__fmul2_rn(ir2, ir6), __ffma2_rn(c12, ir6, mc6));
+  fr.x = r2.x < cut.x ? fr.x : 0.f;
+  fr.y = r2.y < cut.y ? fr.y : 0.f;
+  const float2 tx = __fmul2_rn(fr, dx);
+  fx = __fadd2_rn(fx, tx);
+  fy = __ffma2_rn(fr, dy, fy);
+  fz = __ffma2_rn(fr, dz, fz);
+  vir = __ffma2_rn(tx, dz, vir);
 }
 
 // DPD (Eqs. 6-8, read as the fluctuation-dissipation form): the dissipative
@@ -728,9 +733,13 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   } else {
     if (active) pi = b.p[i];
   }
-  // FP32 LJ constants for separations in units of 2^-S
+  // FP32 LJ constants for separations in units of 2^-S, and the two-lane
+  // partial sums of the paired pair loop
   const float s2S = __int_as_float((127 + 2 * g.qshift) << 23);   // 2^2S
   const float rc2q = (float)K.rc2 * s2S;
+  const float2 cut2 = make_float2(rc2q, rc2q), s2S2 = make_float2(s2S, s2S);
+  const float2 c12_2 = make_float2((float)c12, (float)c12), mc6_2 = make_float2(-(float)c6, -(float)c6);
+  float2 fx2 = make_float2(0.f, 0.f), fy2 = fx2, fz2 = fx2, vir2 = fx2;
   V4<R> vi = make4<R>(R(0), R(0), R(0), R(0));
   int gi = 0;
   if (DPD && active) {
@@ -762,18 +771,27 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
 #pragma unroll
         for (int u = 0; u < U; ++u) q[u] = __ldg(b.q + entry_index(e[u]));
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          lj_pair_q(GQ, q[u], e[u], rc2q, s2S, c12, c6, fx, fy, fz, vir);
+        for (int u = 0; u < U; u += 2)
+          lj_pair2_q(GQ, q[u], q[u + 1], e[u], e[u + 1], cut2, s2S2, c12_2, mc6_2, fx2, fy2,
+                     fz2, vir2);
         if constexpr (DPD) {
 #pragma unroll
           for (int u = 0; u < U; ++u)
             dpd_pair<R>(g, pi, vi, gi, b, e[u], G, GQ, n1, rc2, tdx, tdy, tdz);
         }
       }
-      for (; r < rn; ++r) {
-        const uint32_t e = rows[r][lane];
-        lj_pair_q(GQ, __ldg(b.q + entry_index(e)), e, rc2q, s2S, c12, c6, fx, fy, fz, vir);
-        if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, GQ, n1, rc2, tdx, tdy, tdz);
+      for (; r < rn; r += 2) {
+        // the last pair of an odd count goes with a dropped copy of itself
+        const bool two = r + 1 < rn;
+        const uint32_t ea = rows[r][lane], eb = two ? rows[r + 1][lane] : ea;
+        const int4 qa = __ldg(b.q + entry_index(ea));
+        const int4 qb = two ? __ldg(b.q + entry_index(eb)) : qa;
+        lj_pair2_q(GQ, qa, qb, ea, eb, make_float2(rc2q, two ? rc2q : 0.f), s2S2, c12_2,
+                   mc6_2, fx2, fy2, fz2, vir2);
+        if constexpr (DPD) {
+          dpd_pair<R>(g, pi, vi, gi, b, ea, G, GQ, n1, rc2, tdx, tdy, tdz);
+          if (two) dpd_pair<R>(g, pi, vi, gi, b, eb, G, GQ, n1, rc2, tdx, tdy, tdz);
+        }
       }
     } else {
       for (; r + U <= rn; r += U) {
@@ -813,11 +831,11 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   }
 
   if constexpr (sizeof(R) == 4) {
-    // the pair sums were taken in units of 2^S (force) and 2^2S (virial)
-    fx *= GQ.inv;
-    fy *= GQ.inv;
-    fz *= GQ.inv;
-    vir *= GQ.inv * GQ.inv;
+    // the two lanes' pair sums, taken in units of 2^S (force) and 2^2S (virial)
+    fx = (fx2.x + fx2.y) * GQ.inv;
+    fy = (fy2.x + fy2.y) * GQ.inv;
+    fz = (fz2.x + fz2.y) * GQ.inv;
+    vir = (vir2.x + vir2.y) * (GQ.inv * GQ.inv);
   }
   // separation of o (at po; fixed-point copy qo) from the image of the
   // particle that bond entry e names, in length units
@@ -1308,90 +1326,132 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 }
 
 // ------------------------------------------------------------- rebuild: list
-// LE-aware Verlet list from the build positions.  Neighbour cells of cell
-// (cx,cy,cz): for a y/z neighbour row inside the box, the x cells cx-1..cx+1;
-// for a row across the top/bottom face, the x window shifted by the image
-// offset: 3 or 4 cells covering every cell within rl of the shifted row
-// (f_build/lx decides whether the window reaches a 4th cell).  Rows and
-// cells whose box lies farther than rl from the particle are skipped.
+// LE-aware Verlet list from the build positions, one warp per 32 consecutive
+// cell-sorted particles: the same 32 particles whose list rows the pair
+// kernel streams (entry k of lane l is row k, column l of the warp's tile).
+//
+// The warp's particles sit in a few consecutive cells, usually of one cell
+// row (cy, cz).  For each group of lanes that share a home row, the union of
+// their neighbour cells in a neighbour row (dcy, dcz) is one range of x cells:
+// xa - 1 .. xb + 1 for a row inside the box, and for a row across the
+// top/bottom face the window shifted by the image offset at the build (m_b
+// cells plus f_b; 3 or 4 cells per home cell).  The candidates of that range
+// are staged 32 at a time in shared memory -- coalesced loads, each moved into
+// the group's frame by the lane that loads it -- and every lane of the group
+// tests every staged candidate from the broadcast copy.  A candidate within
+// the list radius is stored with the slot of its image as seen from the
+// lane's own cell.  Rows that no lane of the group reaches are skipped.
 template <class R, class BX>
 __device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                              Bufs<R> s1, Work w, int target_cur, BX bx) {
-  __shared__ float s_offx[kNumSlots];
-  for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
-  __syncthreads();
+  __shared__ float4 s_cand[kListMaxThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int i = bx() * blockDim.x + threadIdx.x;
+  const bool active = i < g.n;
+  const float4 qi = active ? b.pb[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  int cx = 0, cy = 0, cz = 0;
+  if (active) cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
+  const int nc0 = g.nc[0], nc1 = g.nc[1], nc2 = g.nc[2];
+  const float lx = (float)g.lc[0], ly = (float)g.lc[1], lz = (float)g.lc[2];
+  const float rl2 = g.rl2_build;
+  const float hy = g.half_lc_f[1], hz = g.half_lc_f[2];
+  const int mb = d->m_build;
+  const float fb = (float)d->f_build;
+  const int maxnb = g.maxnb;
+  uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)maxnb * 32u + lane;
+  const uint32_t self = make_entry(i, slot_code(0, 0, 0, 0));
   int cnt = 0;
-  if (i < g.n) {
-    const float4 qi = b.pb[i];
-    int cx, cy, cz;
-    cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
-    const float rl2 = g.rl2_build;
-    const float hx = g.half_lc_f[0], hy = g.half_lc_f[1], hz = g.half_lc_f[2];
-    const float ly = (float)g.lc[1], lz = (float)g.lc[2];
-    const int mb = d->m_build;
-    uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
+  const int row_i = active ? cy + nc1 * cz : -1;
+  unsigned pending = __ballot_sync(0xffffffffu, active);
+  while (pending) {
+    const int row0 = __shfl_sync(0xffffffffu, row_i, __ffs(pending) - 1);
+    const bool mine = row_i == row0;
+    pending &= ~__ballot_sync(0xffffffffu, mine);
+    const int xa = __reduce_min_sync(0xffffffffu, mine ? cx : 0x7fffffff);
+    const int xb = __reduce_max_sync(0xffffffffu, mine ? cx : -0x7fffffff);
+    const int gcy = row0 % nc1, gcz = row0 / nc1;
+    // the lane's position in the frame of the group's first cell, and its
+    // cell offset from that cell (added to a staged entry, it gives the slot)
+    const float xi = fmaf((float)(cx - xa), lx, qi.x);
+    const uint32_t kbase = (uint32_t)(cx - xa);
     for (int dcz = -1; dcz <= 1; ++dcz) {
-      const float az = qi.z + (float)dcz * lz;
-      const float gz = fmaxf(fabsf(az) - hz, 0.f);
-      if (gz * gz >= rl2) continue;
-      int czj = cz - dcz, cross = 0;
-      if (czj < 0) { czj += g.nc[2]; cross = 1; }
-      else if (czj >= g.nc[2]) { czj -= g.nc[2]; cross = 1; }
+      const float gz = fmaxf(fabsf(qi.z + (float)dcz * lz) - hz, 0.f);
+      if (!__any_sync(0xffffffffu, mine && gz * gz < rl2)) continue;
+      int czj = gcz - dcz, cross = 0;
+      if (czj < 0) { czj += nc2; cross = 1; }
+      else if (czj >= nc2) { czj -= nc2; cross = 1; }
       int kmin = -1, kmax = 1;
       if (cross) {
         kmin = d->win_lo[dcz > 0 ? 1 : 0];
         kmax = d->win_hi[dcz > 0 ? 1 : 0];
       }
+      const int sh = cross ? dcz * mb : 0;           // whole cells of the image offset
+      const float xsh = cross ? (float)dcz * fb : 0.f; // its remainder
+      const float zoff = (float)dcz * lz;
       for (int dcy = -1; dcy <= 1; ++dcy) {
-        const float ay = qi.y + (float)dcy * ly;
-        const float gy = fmaxf(fabsf(ay) - hy, 0.f);
-        const float gyz = gy * gy + gz * gz;
-        if (gyz >= rl2) continue;
-        const int cyj = wrap_index(cy - dcy, g.nc[1]);
-        const int rowbase = g.nc[0] * (cyj + g.nc[1] * czj);
-        for (int k = kmin; k <= kmax; ++k) {
-          const int slot = slot_code(k, dcy, dcz, cross);
-          const float ax = qi.x + s_offx[slot];
-          const float gx = fmaxf(fabsf(ax) - hx, 0.f);
-          if (gx * gx + gyz >= rl2) continue;
-          const int cxj = wrap_index(cx - k + (cross ? dcz * mb : 0), g.nc[0]);
-          const int cj = rowbase + cxj;
+        const float gy = fmaxf(fabsf(qi.y + (float)dcy * ly) - hy, 0.f);
+        if (!__any_sync(0xffffffffu, mine && gy * gy + gz * gz < rl2)) continue;
+        const int cyj = wrap_index(gcy - dcy, nc1);
+        const int base = nc0 * (cyj + nc1 * czj);
+        const float yoff = (float)dcy * ly;
+        // slot fields of this row, the x field's bias 3 included
+        const uint32_t fields = (uint32_t)slot_code(0, dcy, dcz, cross);
+        // candidate x cells, unwrapped: a home cell cx takes cx - k + sh for
+        // k in [kmin, kmax]; taken in runs that do not cross the periodic x face
+        int u = xa - kmax + sh;
+        const int uend = xb - kmin + sh;
+        while (u <= uend) {
+          const int c0 = wrap_index(u, nc0);
+          const int len = min(uend - u + 1, nc0 - c0);
+          // a candidate in x cell cxj of this run sits m = cxj + mshift cells
+          // from the group's first cell in the image frame: k = (cx - xa) - m
+          const int mshift = u - c0 - sh - xa;
           // clamped so that a corrupt range can never leave the particle arrays
-          const int j0 = min(max(w.cell_start[cj], 0), g.n);
-          const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
-          const bool self_slot = (slot == slot_code(0, 0, 0, 0));
-          const uint32_t tag = (uint32_t)slot;
-          int j = j0;
-          auto emit = [&](int jj, const float4 &q) {
-            const float dx = ax - q.x, dy = ay - q.y, dz = az - q.z;
-            if (dx * dx + dy * dy + dz * dz < rl2 && !(self_slot && jj == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = ((uint32_t)jj << kSlotBits) | tag;
-              ++cnt;
+          const int j0 = min(max(w.cell_start[base + c0], 0), g.n);
+          const int j1 = min(max(w.cell_start[base + c0 + len], j0), g.n);
+          for (int jb = j0; jb < j1; jb += 32) {
+            const int jj = jb + lane;
+            if (jj < j1) {
+              const float4 q = __ldg(b.pb + jj);
+              const int m = (__float_as_int(q.w) - base) + mshift;
+              // the entry for a lane in the group's first cell (k = -m); a
+              // lane adds its own cell offset
+              const uint32_t e0 = make_entry(jj, 0) + fields - (uint32_t)m;
+              s_cand[warp][lane] = make_float4(fmaf((float)m, lx, q.x) - xsh, q.y - yoff,
+                                               q.z - zoff, __uint_as_float(e0));
             }
-          };
-          // kListUnroll candidates per pass: their loads are in flight together
-          for (; j + kListUnroll <= j1; j += kListUnroll) {
-            float4 q[kListUnroll];
-#pragma unroll
-            for (int u = 0; u < kListUnroll; ++u) q[u] = __ldg(b.pb + j + u);
-#pragma unroll
-            for (int u = 0; u < kListUnroll; ++u) emit(j + u, q[u]);
+            __syncwarp();
+            const int nj = min(32, j1 - jb);
+            if (mine) {
+#pragma unroll 4
+              for (int c = 0; c < nj; ++c) {
+                const float4 cq = s_cand[warp][c];
+                const float dx = xi - cq.x, dy = qi.y - cq.y, dz = qi.z - cq.z;
+                const uint32_t e = __float_as_uint(cq.w) + kbase;
+                if (dx * dx + dy * dy + dz * dz < rl2 && e != self) {
+                  out[min(cnt, maxnb - 1) * 32] = e;
+                  ++cnt;
+                }
+              }
+            }
+            __syncwarp();
           }
-          for (; j < j1; ++j) emit(j, __ldg(b.pb + j));
+          u += len;
         }
       }
     }
+  }
+  if (active) {
     w.ncount[i] = cnt;
     atomicMax(&d->list_max, cnt);
-    if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
+    if (cnt > maxnb) atomicOr(&d->err, (int)kErrCapacity);
   }
   // total list entries (for the mean list length), one atomic per block
   __shared__ unsigned long long s_tot[kListMaxThreads / 32];
   const unsigned long long c = warp_sum((unsigned long long)cnt);
-  if ((threadIdx.x & 31) == 0) s_tot[threadIdx.x >> 5] = c;
+  if (lane == 0) s_tot[warp] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;

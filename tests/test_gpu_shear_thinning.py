@@ -8,7 +8,10 @@ block-averaged error, plus the steady-state energy balance that ties the
 stress to the temperature: the shear work <sigma_xz> shear_rate V equals
 what the Langevin thermostat removes, 3 N xi (T_pec - kT).  (At the highest
 rate that balance sets T_pec near 3: viscous heating.)  The rates run
-together as one batch, FP32 forces."""
+together as one batch, FP32 forces.  The melt is prepared at rest with
+dt = 0.01; under shear the step is dt = 0.005, since at T_pec ~ 3 the
+0.01 step lets a fast WCA collision throw a bead past the FENE limit R0
+(a broken bond) once in a while."""
 import numpy as np
 import pytest
 
@@ -23,8 +26,8 @@ RATES = (0.01, 0.1, 1.0)
 XI = 0.5
 
 
-def _melt(gd, pos, vel, box, bonds, seed):
-    sim = le.Sim(box, gd, RC, 0.3, dt=0.01, xi=XI, seed=seed, system_id=seed,
+def _melt(gd, pos, vel, box, bonds, seed, dt=0.01):
+    sim = le.Sim(box, gd, RC, 0.3, dt=dt, xi=XI, seed=seed, system_id=seed,
                  precision=1, angle_k=1.5, sample_every=1)
     sim.set_bonds(bonds)
     sim.set_particles(pos, vel)
@@ -68,12 +71,12 @@ def test_kremer_grest_melt_thins_under_shear():
     for m, gd in enumerate(RATES):
         v = vel.copy()
         v[:, 0] += gd * (pos[:, 2] - 0.5 * box)
-        sims.append(_melt(gd, pos, v, box, bonds, 100 + m))
+        sims.append(_melt(gd, pos, v, box, bonds, 100 + m, dt=0.005))
     with le.Batch() as b:
         for s in sims:
             b.add(s)
-        b.step(10000)  # start-up transient
-        sxz, tpe = _block_means(sims, b, 8, 5000)
+        b.step(20000)  # start-up transient (100 time units)
+        sxz, tpe = _block_means(sims, b, 8, 10000)
     for s in sims:
         s.close()
     rates = np.array(RATES)
