@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--systems", type=int, default=256, help="batched workload: box count")
     ap.add_argument("--angle-k", type=float, default=0.0,
                     help="kg workload: bending constant k_a of Eq. 12 (0: WCA + FENE only)")
+    ap.add_argument("--kg-equilibrate", type=int, default=5000,
+                    help="kg workload: uncapped steps at rest after the push-off (untimed)")
     ap.add_argument("--no-plain", action="store_true",
                     help="batched workload: time the batch alone (no per-box comparison, "
                          "no tuning), for profiler captures")
@@ -267,12 +269,18 @@ class ClockSampler:
 
 
 def force_kernel_bytes(n: int, mean_nb: float) -> float:
-    """Algorithmic HBM bytes of one pair-force launch (FP32 mode): per
-    particle own position 16 + list count 4 + 4 per list entry + half-step
-    velocity 16 + particle id 4 (random-force counter), writes conservative
-    force 16 + total force 16 + velocity 16.  Neighbour positions are gathered
-    from cache (counted once in the own-position read)."""
-    return n * (16 + 4 + 4 * mean_nb + 16 + 4 + 16 + 16 + 16)
+    """Algorithmic HBM bytes of one pair-force evaluation (the K4 count):
+    per particle its own position 16 + list count 4 + 4 per list entry +
+    the force written 16.  Neighbour positions are gathered from cache
+    (counted once in the own-position read)."""
+    return n * (16 + 4 + 4 * mean_nb + 16)
+
+
+def force_launch_bytes(n: int, mean_nb: float) -> float:
+    """The same launch's bytes with its fused epilogue (Langevin, second half
+    kick, samples): + half-step velocity 16 + particle id 4 read, total force
+    16 and velocity 16 written."""
+    return force_kernel_bytes(n, mean_nb) + n * (16 + 4 + 16 + 16)
 
 
 def measured_peak():
@@ -371,6 +379,7 @@ def run_ours(args):
     kbytes = force_kernel_bytes(w.n, mean_nb)
     f_avg_s = force_ms / args.steps * 1e-3
     achieved = kbytes / f_avg_s / 1e9
+    achieved_fused = force_launch_bytes(w.n, mean_nb) / f_avg_s / 1e9
     peak, peak_kind = measured_peak()
     traffic_pp = profiled_traffic(os.path.join(ROOT, "paper_2109_11083_gb300", "csrc",
                                                "le_kernels.cu"))
@@ -436,6 +445,8 @@ def run_ours(args):
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "k_force (pair force + Langevin + kick + samples)",
                          "algorithmic_bytes_per_launch": kbytes,
+                         "bytes_count": "pair force alone: (16 + 4 + 4 n_list + 16) B per particle",
+                         "achieved_with_fused_epilogue": achieved_fused,
                          "avg_launch_ms": f_avg_s * 1e3,
                          "traffic": (traffic_pp * w.n if traffic_pp else None)},
             "kernel_ms_per_step": {"k_force": force_ms / args.steps,
@@ -602,19 +613,31 @@ def le_min_image(d, box, dX):
 
 
 def run_kg(args):
-    """A Kremer-Grest melt of 200 chains x 100 beads (WCA + FENE,
-    optional Eq. 12 bending with --angle-k), FP32 forces, dt 0.01, shear rate
-    1e-3, Langevin xi 0.5.  The chains start on a serpentine lattice path at
-    the bead density 0.85 (bond 1.02, no overlaps), so no push-off is needed."""
+    """A Kremer-Grest melt of 200 chains x 100 beads (WCA + FENE, optional
+    Eq. 12 bending with --angle-k), FP32 forces, dt 0.01, shear rate 1e-3,
+    Langevin xi 0.5.  The initial condition is the stated one: freely jointed
+    random walks of bond length 0.97, a force-capped push-off (FP64; caps 10,
+    30, 100, 300, 1000, 400 steps each, dt 0.005, at rest), then an uncapped
+    equilibration at rest (--kg-equilibrate steps, FP32) -- none of it timed."""
     import torch
     import paper_2109_11083_gb300 as le
+    from paper_2109_11083_gb300 import prepare
     torch.cuda.set_device(0)
     w = synth.kg_melt_200x100()
-    k = math.ceil(w.n ** (1 / 3) - 1e-9)
-    pos, box, bonds = synth.lattice_chains(w.nchains, w.nbeads, w.rho * k ** 3 / w.n, w.seed)
-    vel = synth.mb_velocities(w.n, w.kT, w.seed)
-    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * box)
+    pos, box, bonds = synth.random_walk_chains(w.nchains, w.nbeads, w.rho, w.seed)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    pos, vel = prepare.push_off(pos, box, bonds, seed=w.seed, stream=stream.cuda_stream)
+    eq = le.Sim(box, 0.0, w.rc, w.skin, stream=stream.cuda_stream, dt=w.dt, xi=w.xi, kT=w.kT,
+                fene_k=w.fene_k, fene_R0=w.fene_R0, seed=w.seed + 1, system_id=1,
+                precision=le.LE_FP32, sample_every=0, angle_k=args.angle_k)
+    eq.set_bonds(bonds)
+    eq.set_particles(pos, vel)
+    eq.step(args.kg_equilibrate)
+    pos, vel = eq.positions()
+    eq.close()
+    t_prep = time.perf_counter() - t0
+    vel[:, 0] += w.shear_rate * (pos[:, 2] - 0.5 * box)
     sim = le.Sim(box, w.shear_rate, w.rc, w.skin, stream=stream.cuda_stream, dt=w.dt, xi=w.xi,
                  kT=w.kT, fene_k=w.fene_k, fene_R0=w.fene_R0, seed=w.seed, system_id=1,
                  precision=le.LE_FP32, sample_every=1, angle_k=args.angle_k)
@@ -644,7 +667,11 @@ def run_kg(args):
                        "beads_per_chain": w.nbeads, "density": w.rho, "box": round(box, 6),
                        "rc": w.rc, "skin": w.skin, "fene_k": w.fene_k, "fene_R0": w.fene_R0,
                        "angle_k": args.angle_k, "shear_rate": w.shear_rate, "dt": w.dt,
-                       "langevin_xi": w.xi, "kT": w.kT, "start": "serpentine lattice path",
+                       "langevin_xi": w.xi, "kT": w.kT,
+                       "start": (f"random walks (bond 0.97), capped push-off "
+                                 f"{list(prepare.PUSH_OFF_CAPS)} x {prepare.PUSH_OFF_STEPS} steps "
+                                 f"(FP64), {args.kg_equilibrate} steps at rest; "
+                                 f"{t_prep:.1f} s, untimed"),
                        "launch_shapes": {"force_threads": tuned[0], "list_threads": tuned[1]}},
             "rebuilds": c1["rebuilds"] - c0["rebuilds"],
             "chains": {"R_ee2_mean": float((ree ** 2).sum(axis=1).mean()),

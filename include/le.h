@@ -100,12 +100,16 @@ typedef struct le_params {
     double angle_k;           /* k_a of the chain bending term (Eq. 12, read as
                                  k_a (1 + cos theta), theta the angle at the middle
                                  bead of two bonds); 0: none; used only with bonds */
+    double force_cap;         /* > 0: each LJ pair force is limited to this magnitude
+                                 (the push-off of overlapping random-walk chains
+                                 before a melt is integrated; not part of Eqs. 9-13);
+                                 LE_FP64 only; 0: none */
 } le_params;
 
 /* Fills *p with defaults: eps = sigma = mass = kT = xi = 1, dt = 0.005,
  * lj_shift = 1, thermostat = LE_THERMO_PECULIAR, fene_k = 30, fene_R0 = 1.5,
  * precision = LE_FP64, seed = 0, system_id = 0, sample_every = 1,
- * profile_bins = 20. */
+ * profile_bins = 20, angle_k = 0, force_cap = 0. */
 LE_API void le_default_params(le_params *p);
 
 /* Creates a handle for the box [0,box[0]) x [0,box[1]) x [0,box[2]) sheared at
@@ -291,7 +295,7 @@ LE_API const char *le_batch_last_error(const le_batch *b);
  * step `step`, whose image offset is dX(step) of Eq. 4) written to forces
  * (n x 3, host), for the box, shear rate, rc, skin and parameters of
  * le_create (precision selects FP64 or FP32 arithmetic; the thermostat,
- * bond and sampling fields are ignored).  No handle is needed.
+ * bond, sampling and force_cap fields are ignored).  No handle is needed.
  * The paper has no counterpart to this entry point.  It exists for callers
  * that cannot call cudaMalloc where they need forces: a loop that must not
  * allocate device memory (or meet an out-of-memory error) once it runs, or a

@@ -60,6 +60,7 @@ class Params(C.Structure):
         ("system", C.c_uint64),
         ("nbins", C.c_int),
         ("angle_k", C.c_double),
+        ("force_cap", C.c_double),
     ]
 
 
@@ -128,7 +129,7 @@ def lib():
 
 def params(box, shear_rate, rc, *, eps=1.0, sigma=1.0, lj_shift=1, fene_k=0.0,
            fene_R0=1.5, mass=1.0, kT=1.0, xi=1.0, dt=0.005, thermostat=1,
-           seed=0, system=0, nbins=20, angle_k=0.0) -> Params:
+           seed=0, system=0, nbins=20, angle_k=0.0, force_cap=0.0) -> Params:
     b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
     p = Params()
     p.L = (C.c_double * 3)(*b)
@@ -137,6 +138,7 @@ def params(box, shear_rate, rc, *, eps=1.0, sigma=1.0, lj_shift=1, fene_k=0.0,
     p.mass, p.kT, p.xi, p.dt, p.thermostat = mass, kT, xi, dt, thermostat
     p.seed, p.system, p.nbins = seed, system, nbins
     p.angle_k = angle_k
+    p.force_cap = force_cap
     return p
 
 

@@ -44,6 +44,9 @@ typedef struct {
     uint64_t seed, system;
     int    nbins;         /* velocity-profile bins along z */
     double angle_k;       /* k_a of the bending term of Eq. 12 (0: none) */
+    double force_cap;     /* > 0: LJ pair force magnitude limited to this value (the
+                             push-off of overlapping initial chains, not part of the
+                             method; energies stay those of Eq. 9/10) */
 } ora_params;
 
 enum { ORA_OK = 0, ORA_BOND_BROKEN = 1, ORA_BOX_TOO_SMALL = 2, ORA_NONFINITE = 3 };
@@ -260,6 +263,11 @@ static void pair_visit(void *vctx, int64_t i, int64_t j)
     if (!(r2 < c->p->rc * c->p->rc)) return;
     double e;
     double fr = lj_f_over_r(c->p, r2, &e);
+    if (c->p->force_cap > 0.0) {   /* |F| = |f/r| r at most force_cap */
+        double lim = c->p->force_cap / sqrt(r2);
+        if (fr > lim) fr = lim;
+        if (fr < -lim) fr = -lim;
+    }
     for (int a = 0; a < 3; ++a) c->F[3 * i + a] += fr * d[a];
     if (i < j) {  /* each unordered pair once in the energy and the virial */
         c->epot += e;

@@ -49,6 +49,7 @@ class le_params(C.Structure):
         ("seed", C.c_uint64), ("system_id", C.c_uint64),
         ("sample_every", C.c_int), ("profile_bins", C.c_int),
         ("angle_k", C.c_double),
+        ("force_cap", C.c_double),
     ]
 
 

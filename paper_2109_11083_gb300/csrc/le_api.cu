@@ -226,7 +226,7 @@ void choose_cells(le_sim *s) {
   int bits = 1;
   while ((1ll << bits) < (long long)g.ncell) ++bits;
   g.sort_bits = bits;
-  s->s.sort_passes = sort_passes_for(bits);
+  s->s.sort_passes = sort_passes_for(g.sort_bits);
   set_fixed_point(g);
 }
 
@@ -273,6 +273,7 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
     c.R02 = p->fene_R0 * p->fene_R0;
     c.fene_k = p->fene_k;
     c.ang_k = p->angle_k;
+    g.force_cap = p->force_cap;
     c.dpd_xi = p->xi;
     c.dpd_amp = std::sqrt(24.0 * p->kT * p->xi / p->dt);
     c.inv_rc = 1.0 / rc;
@@ -494,6 +495,8 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
   if (p->profile_bins < 1 || p->profile_bins > kMaxBins) return LE_ERR_INVALID_ARG;
   if (p->precision != LE_FP64 && p->precision != LE_FP32) return LE_ERR_INVALID_ARG;
   if (p->thermostat < LE_THERMO_NONE || p->thermostat > LE_THERMO_DPD) return LE_ERR_INVALID_ARG;
+  if (!(p->force_cap >= 0.0) || (p->force_cap > 0.0 && p->precision != LE_FP64))
+    return LE_ERR_INVALID_ARG;
   const double rl = rc + skin;
   for (int a = 0; a < 3; ++a)
     if (!(rl < 0.5 * box[a])) return LE_ERR_BOX_TOO_SMALL;

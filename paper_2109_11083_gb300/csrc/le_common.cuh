@@ -121,6 +121,7 @@ struct Geom {
   double shear_rate, dt, mass, kT, xi;
   double rc, skin, rl;            // rl = list radius (rc + skin)
   double eps, sigma, fene_k, fene_R0;
+  double force_cap;               // > 0: LJ pair force magnitude limit (FP64 kernels)
   double lc[3];                   // cell edge
   int nc[3];                      // cells per dimension
   int ncell;

@@ -499,7 +499,7 @@ template <> __device__ __forceinline__ float recip<float>(float x) {
 
 template <class R>
 __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32_t e,
-                                        const SlotGeo<R> &G, R rc2, R c12, R c6,
+                                        const SlotGeo<R> &G, R rc2, R c12, R c6, R cap,
                                         R &fx, R &fy, R &fz, R &vir) {
   R dx, dy, dz;
   slot_sep<R>(e, G, pi, pj, dx, dy, dz);
@@ -510,7 +510,12 @@ __device__ __forceinline__ void lj_pair(const V4<R> &pi, const V4<R> &pj, uint32
   const R ir2 = recip<R>(r2);
   const R ir6 = ir2 * ir2 * ir2;
   // 24 eps (2 (sigma/r)^12 - (sigma/r)^6) / r^2 = ir2 ir6 (c12 ir6 - c6)
-  const R fr = r2 < rc2 ? ir2 * ir6 * fma(c12, ir6, -c6) : R(0);
+  R fr = r2 < rc2 ? ir2 * ir6 * fma(c12, ir6, -c6) : R(0);
+  // push-off: |F| = |fr| r limited to cap (FP64 kernels only)
+  if (cap > R(0)) {
+    const R lim = cap / sqrt(r2);
+    fr = fr > lim ? lim : (fr < -lim ? -lim : fr);
+  }
   const R tx = fr * dx;
   fx += tx;
   fy += fr * dy;
@@ -719,6 +724,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   // c6 = 24 eps sigma^6, c12 = 48 eps sigma^12
   const R sig6 = K.sig2 * K.sig2 * K.sig2;
   const R c6 = K.eps24 * sig6, c12 = R(2) * c6 * sig6;
+  const R cap = sizeof(R) == 8 ? R(g.force_cap) : R(0);
   R fx = R(0), fy = R(0), fz = R(0), vir = R(0);
   R tdx = R(0), tdy = R(0), tdz = R(0);  // DPD pair forces
   V4<R> pi = make4<R>(R(0), R(0), R(0), R(0));
@@ -803,7 +809,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
         for (int u = 0; u < U; ++u) q[u] = load4(b.p + entry_index(e[u]));
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          lj_pair<R>(pi, q[u], e[u], G, rc2, c12, c6, fx, fy, fz, vir);
+          lj_pair<R>(pi, q[u], e[u], G, rc2, c12, c6, cap, fx, fy, fz, vir);
         if constexpr (DPD) {
 #pragma unroll
           for (int u = 0; u < U; ++u)
@@ -813,7 +819,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       for (; r < rn; ++r) {
         const uint32_t e = rows[r][lane];
         const V4<R> q = load4(b.p + entry_index(e));
-        lj_pair<R>(pi, q, e, G, rc2, c12, c6, fx, fy, fz, vir);
+        lj_pair<R>(pi, q, e, G, rc2, c12, c6, cap, fx, fy, fz, vir);
         if constexpr (DPD) dpd_pair<R>(g, pi, vi, gi, b, e, G, GQ, n1, rc2, tdx, tdy, tdz);
       }
     }

@@ -317,3 +317,22 @@ def test_peculiar_langevin_gives_a_linear_profile_and_positive_viscosity():
     assert slope == pytest.approx(gd, rel=0.05)
     eta = s.samples.sxz_sum / s.samples.nsamples / gd
     assert 0.5 < eta < 10.0
+
+
+def test_force_cap_limits_each_pair_force_to_the_cap():
+    """The push-off cap: an overlapping pair feels exactly the cap along the
+    separation; a pair whose Eq. 9 force is below the cap is unchanged."""
+    box = 12.0
+    cap = 25.0
+    pos = np.array([[3.0, 3.0, 3.0], [3.3, 3.4, 3.0], [8.0, 8.0, 8.0], [9.2, 8.0, 8.0]])
+    p = oracle.params(box, 0.0, 2.5, force_cap=cap)
+    _, F, _, _ = oracle.forces(p, 0.0, pos, use_cells=False)
+    d = pos[0] - pos[1]
+    assert np.allclose(F[0], cap * d / np.linalg.norm(d), rtol=1e-13)
+    assert np.allclose(F[1], -F[0], rtol=1e-13)
+    _, F0, _, _ = oracle.forces(oracle.params(box, 0.0, 2.5), 0.0, pos, use_cells=False)
+    r = 1.2
+    f = 24.0 * (2 * r ** -12 - r ** -6) / r     # Eq. 9 force at r = 1.2 (below the cap)
+    assert abs(f) < cap
+    assert np.allclose(F[2:], F0[2:], rtol=1e-14)
+    assert F0[3, 0] == pytest.approx(f, rel=1e-12)
