@@ -372,15 +372,10 @@ constexpr int kForceWarps = kForceThreads / 32;
 #define LE_FORCE_MINB32 4
 #endif
 constexpr int kForceUnroll = LE_FORCE_UNROLL;
-// candidate loads in flight per thread in the list build, and its resident
-// blocks of the largest shape per SM
-#ifndef LE_LIST_UNROLL
-#define LE_LIST_UNROLL 6
-#endif
+// resident blocks of the largest list-build shape per SM
 #ifndef LE_LIST_MINB
 #define LE_LIST_MINB 4
 #endif
-constexpr int kListUnroll = LE_LIST_UNROLL;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -419,9 +414,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // and the cross-face shift s of this step: a handful of ALU operations.
 template <class R> struct SlotGeo {
   R lx, ly, lz, s;
-  // FP32 decode: the fields sit at bits 0, 3 and 5, so their raw values carry
-  // factors 1, 8 and 32, taken out exactly by these power-of-two scalings
-  R ly8, lz32, s32;
 };
 template <class R>
 __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &ox, R &oy, R &oz) {
@@ -435,30 +427,6 @@ __device__ __forceinline__ void slot_offset(uint32_t e, const SlotGeo<R> &G, R &
   oz = R(dcz) * G.lz;
 }
 
-// FP32: a slot field f at bit b becomes the float 2^b f as (2^23 + 2^b f) -
-// 2^23, built with one integer AND-OR into the bits of 2^23 and one float
-// subtraction (no shift, no conversion instruction); the field's bias folds
-// into the subtracted constant and the 2^b into the pre-scaled cell edge.
-struct SlotF {
-  float k, dcy8, dcz32, cz32;  // k, 8 dcy, 32 dcz, 32 cz
-};
-__device__ __forceinline__ SlotF slot_fields(uint32_t e) {
-  SlotF f;
-  f.k = __uint_as_float(0x4B000000u | (e & 0x07u)) - 8388611.0f;       // -3..4
-  f.dcy8 = __uint_as_float(0x4B000000u | (e & 0x18u)) - 8388616.0f;    // 8 x (-1..1)
-  f.dcz32 = __uint_as_float(0x4B000000u | (e & 0x60u)) - 8388640.0f;   // 32 x (-1..1)
-  f.cz32 = (e & 0x80u) ? f.dcz32 : 0.0f;
-  return f;
-}
-template <>
-__device__ __forceinline__ void slot_offset<float>(uint32_t e, const SlotGeo<float> &G, float &ox,
-                                                   float &oy, float &oz) {
-  const SlotF f = slot_fields(e);
-  ox = __fmaf_rn(f.cz32, G.s32, f.k * G.lx);
-  oy = f.dcy8 * G.ly8;
-  oz = f.dcz32 * G.lz32;
-}
-
 // Separation d = p_i - (p_j + image offset of the slot).
 template <class R>
 __device__ __forceinline__ void slot_sep(uint32_t e, const SlotGeo<R> &G, const V4<R> &pi,
@@ -468,19 +436,6 @@ __device__ __forceinline__ void slot_sep(uint32_t e, const SlotGeo<R> &G, const 
   dx = (pi.x - pj.x) + ox;
   dy = (pi.y - pj.y) + oy;
   dz = (pi.z - pj.z) + oz;
-}
-
-// FP32: the cell-offset products are fused into the separation (one rounding
-// fewer per component than adding a rounded offset, three instructions fewer
-// per pair); mirrored slots still give exactly d_ji = -d_ij.
-template <>
-__device__ __forceinline__ void slot_sep<float>(uint32_t e, const SlotGeo<float> &G,
-                                                const V4<float> &pi, const V4<float> &pj,
-                                                float &dx, float &dy, float &dz) {
-  const SlotF f = slot_fields(e);
-  dx = __fmaf_rn(f.cz32, G.s32, __fmaf_rn(f.k, G.lx, pi.x - pj.x));
-  dy = __fmaf_rn(f.dcy8, G.ly8, pi.y - pj.y);
-  dz = __fmaf_rn(f.dcz32, G.lz32, pi.z - pj.z);
 }
 
 // A per-particle sample value in 2^-30 fixed point (the scale is a power of
@@ -671,26 +626,13 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int cur = d->cur;
   const long long n1 = d->step;
-  // cell edges and cross-face shift in the kernel's precision (the FP32
-  // kernel reads float copies: no FP64 conversion per thread)
+  // cell edges and cross-face shift (the FP64 pair path; the FP32 one works
+  // on the fixed-point copies)
   SlotGeo<R> G;
-  if constexpr (sizeof(R) == 4) {
-    G.lx = g.lc_hi[0];
-    G.ly = g.lc_hi[1];
-    G.lz = g.lc_hi[2];
-    G.s = d->s_f;
-    G.ly8 = G.ly * 0.125f;
-    G.lz32 = G.lz * 0.03125f;
-    G.s32 = G.s * 0.03125f;
-  } else {
-    G.lx = g.lc[0];
-    G.ly = g.lc[1];
-    G.lz = g.lc[2];
-    G.s = d->s;
-    G.ly8 = G.ly * 0.125;
-    G.lz32 = G.lz * 0.03125;
-    G.s32 = G.s * 0.03125;
-  }
+  G.lx = R(g.lc[0]);
+  G.ly = R(g.lc[1]);
+  G.lz = R(g.lc[2]);
+  G.s = R(d->s);
   const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
     for (int b = t; b < 3 * g.nbins; b += blockDim.x) s_prof[b] = 0;
