@@ -50,6 +50,9 @@ struct le_sim {
   bool eager = false;                // launch kernels directly (no graphs)
   bool dry_run = false;              // allocate() only counts bytes
   size_t device_bytes = 0;           // device memory of the particle buffers
+  // layout of the current device allocation (reused when a later
+  // le_set_particles needs the same one): n, list slots, bond slots, cells
+  long long alloc_key[4] = {-1, -1, -1, -1};
   // rollback snapshot of the current buffer set and the dynamic record
   std::vector<void *> snap;
   std::string err;
@@ -92,6 +95,7 @@ template <class T> le_status dalloc(le_sim *s, T **p, size_t count) {
 }
 
 void free_device(le_sim *s) {
+  for (long long &k : s->alloc_key) k = -1;
   if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
   if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
   s->exec_chunk = s->exec_one = nullptr;
@@ -105,6 +109,42 @@ void free_device(le_sim *s) {
 }
 
 size_t vec_bytes(int prec) { return prec == 1 ? sizeof(float4) : sizeof(D4); }
+
+// True for page-locked (or device-visible) host memory, which the copy
+// engines read and write directly; pageable memory goes through the pinned
+// staging buffer.
+bool is_pinned(const void *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged;
+}
+
+// Host -> device copy of n doubles from the caller's array into dst.
+le_status upload(le_sim *s, double *dst, const double *src, size_t n, double *stage_part) {
+  if (is_pinned(src)) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  } else {
+    std::memcpy(stage_part, src, sizeof(double) * n);
+    CK(cudaMemcpyAsync(dst, stage_part, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  }
+  return LE_OK;
+}
+
+// Device -> host copy of n doubles into the caller's array (after a sync
+// for pageable destinations, through the pinned staging buffer).
+le_status download(le_sim *s, double *dst, const double *src, size_t n, double *stage_part) {
+  if (is_pinned(dst)) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+  } else {
+    CK(cudaMemcpyAsync(stage_part, src, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(dst, stage_part, sizeof(double) * n);
+  }
+  return LE_OK;
+}
 
 // Pointers of one buffer set as raw bytes, in a fixed order (for snapshots
 // and checkpoints): p, plo, v, ft, fc, pb, gid.
@@ -136,6 +176,7 @@ le_status read_dyn(le_sim *s) {
 }
 
 le_status status_from_err(le_sim *s, int err) {
+  if (err & kErrInput) return fail(s, LE_ERR_INVALID_ARG, "non-finite input");
   if (err & kErrBond) return fail(s, LE_ERR_BOND_BROKEN, "a FENE bond reached R0 (Eq. 11)");
   if (err & kErrNonfinite) return fail(s, LE_ERR_NONFINITE, "a force or velocity became non-finite");
   if (err & kErrCapacity) return fail(s, LE_ERR_CAPACITY, "neighbour list capacity exceeded");
@@ -148,7 +189,15 @@ le_status status_from_err(le_sim *s, int err) {
 
 // ------------------------------------------------------------- allocation
 le_status allocate(le_sim *s, int64_t n, int maxnb) {
+  const long long key[4] = {n, maxnb, s->s.g.maxb, s->s.g.ncell};
+  if (!s->dry_run && !s->allocs.empty() && std::equal(key, key + 4, s->alloc_key)) {
+    // the same layout: keep every buffer (and the step graphs, whose kernel
+    // arguments are these buffers and the unchanged geometry)
+    s->has_particles = false;
+    return LE_OK;
+  }
   free_device(s);
+  std::copy(key, key + 4, s->alloc_key);
   s->device_bytes = 0;
   Geom &g = s->s.g;
   const int prec = s->s.prec;
@@ -568,9 +617,7 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
   if (!s) return LE_ERR_INVALID_ARG;
   if (n < 1 || n > kMaxParticles || !pos || !vel)
     return fail(s, LE_ERR_INVALID_ARG, "n out of range or null arrays");
-  for (int64_t q = 0; q < 3 * n; ++q)
-    if (!std::isfinite(pos[q]) || !std::isfinite(vel[q]))
-      return fail(s, LE_ERR_INVALID_ARG, "non-finite input");
+  // non-finite coordinates or velocities are found by the import kernel
   // bond table by particle id
   std::vector<int> deg(n, 0);
   for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
@@ -600,10 +647,8 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
     }
     CK(cudaMemcpyAsync(s->s.w.bond_gid, bg.data(), sizeof(int) * bg.size(), cudaMemcpyHostToDevice,
                        s->stream));
-    std::memcpy(s->h_stage, pos, sizeof(double) * 3 * n);
-    std::memcpy(s->h_stage + 3 * n, vel, sizeof(double) * 3 * n);
-    CK(cudaMemcpyAsync(s->s.stage, s->h_stage, sizeof(double) * 6 * n, cudaMemcpyHostToDevice,
-                       s->stream));
+    CKS(upload(s, s->s.stage, pos, 3 * (size_t)n, s->h_stage));
+    CKS(upload(s, s->s.stage + 3 * n, vel, 3 * (size_t)n, s->h_stage + 3 * n));
     le_status st = initialise(s);
     if (st == LE_ERR_CAPACITY && s->err.rfind("grow:", 0) == 0) {
       maxnb = std::stoi(s->err.substr(5));
@@ -757,11 +802,8 @@ LE_API le_status le_forces(le_sim *s, double *out) {
   if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
   launch_export_forces(s->s, s->stream);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(s->h_stage, s->s.stage, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost,
-                     s->stream));
-  CKS(sync(s));
-  std::memcpy(out, s->h_stage, sizeof(double) * 3 * s->n);
-  return LE_OK;
+  CKS(download(s, out, s->s.stage, 3 * (size_t)s->n, s->h_stage));
+  return sync(s);
 }
 
 LE_API le_status le_positions(le_sim *s, double *pos, double *vel) {
@@ -769,12 +811,9 @@ LE_API le_status le_positions(le_sim *s, double *pos, double *vel) {
   if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
   launch_export(s->s, s->stream);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(s->h_stage, s->s.stage, sizeof(double) * 6 * s->n, cudaMemcpyDeviceToHost,
-                     s->stream));
-  CKS(sync(s));
-  if (pos) std::memcpy(pos, s->h_stage, sizeof(double) * 3 * s->n);
-  if (vel) std::memcpy(vel, s->h_stage + 3 * s->n, sizeof(double) * 3 * s->n);
-  return LE_OK;
+  if (pos) CKS(download(s, pos, s->s.stage, 3 * (size_t)s->n, s->h_stage));
+  if (vel) CKS(download(s, vel, s->s.stage + 3 * s->n, 3 * (size_t)s->n, s->h_stage + 3 * s->n));
+  return sync(s);
 }
 
 LE_API le_status le_stress(le_sim *s, double out9[9], double *xz_avg, int64_t *nsamples) {

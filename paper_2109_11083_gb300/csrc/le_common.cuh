@@ -67,6 +67,7 @@ enum ErrBits : int {
   kErrSlot = 8,       // a bonded pair outside the 90-slot window
   kErrTimeout = 16,   // a bounded wait on a bulk copy gave up
   kErrRange = 32,     // a sampled profile value outside its fixed-point range
+  kErrInput = 64,     // a non-finite coordinate or velocity given to the import
 };
 // Range of the per-particle profile values held as 2^-20 fixed point in the
 // per-step integer sums: |vx| and m vy^2 beyond these are reported, not summed.

@@ -1125,8 +1125,14 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
   if (i >= g.n) return;
   double x[3] = {stage[3 * (size_t)i], stage[3 * (size_t)i + 1], stage[3 * (size_t)i + 2]};
   double vx = stage[3 * (size_t)g.n + 3 * (size_t)i];
-  const double vy = stage[3 * (size_t)g.n + 3 * (size_t)i + 1];
-  const double vz = stage[3 * (size_t)g.n + 3 * (size_t)i + 2];
+  double vy = stage[3 * (size_t)g.n + 3 * (size_t)i + 1];
+  double vz = stage[3 * (size_t)g.n + 3 * (size_t)i + 2];
+  // a non-finite input is reported (the call fails) and replaced by zero
+  if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]) && isfinite(vx) && isfinite(vy) &&
+        isfinite(vz))) {
+    atomicOr(&d->err, (int)kErrInput);
+    x[0] = x[1] = x[2] = vx = vy = vz = 0.0;
+  }
   // any number of images away: remove whole boxes along z first
   const double nzf = floor(x[2] / g.L[2]);
   if (nzf != 0.0) {

@@ -420,3 +420,32 @@ def test_profile_value_out_of_range_is_reported_and_rolled_back():
     vx, cnt = sim.velocity_profile()
     assert cnt.sum() == 6 and np.nanmax(vx) == pytest.approx(900.0, rel=1e-6)
     sim.close()
+
+
+def test_set_particles_again_equals_a_fresh_handle():
+    """A second le_set_particles with the same layout reuses the device
+    buffers and step graphs: the run from it equals the same run on a fresh
+    handle bit for bit; a non-finite input fails the call (the import kernel
+    finds it) and leaves the handle usable."""
+    gd = 0.4
+    pos1, vel1, box = lj_inputs(2000, 0.8442, gd, 41)
+    pos2, vel2, _ = lj_inputs(2000, 0.8442, gd, 43)
+    a = le.Sim(box, gd, 2.5, 0.3, seed=9, precision=1)
+    a.set_particles(pos1, vel1)
+    a.step(25)
+    bad = pos2.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(le.LEError) as e:
+        a.set_particles(bad, vel2)
+    assert e.value.status == 1
+    a.set_particles(pos2, vel2)
+    a.step(40)
+    b = le.Sim(box, gd, 2.5, 0.3, seed=9, precision=1)
+    b.set_particles(pos2, vel2)
+    b.step(40)
+    ra, va = a.positions()
+    rb, vb = b.positions()
+    assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+    assert np.array_equal(a.forces(), b.forces())
+    a.close()
+    b.close()
