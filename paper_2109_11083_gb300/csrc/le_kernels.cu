@@ -372,10 +372,15 @@ constexpr int kForceWarps = kForceThreads / 32;
 #define LE_FORCE_MINB32 4
 #endif
 constexpr int kForceUnroll = LE_FORCE_UNROLL;
-// resident blocks of the largest list-build shape per SM
+// candidate loads in flight per thread in the list build, and its resident
+// blocks of the largest shape per SM
+#ifndef LE_LIST_UNROLL
+#define LE_LIST_UNROLL 6
+#endif
 #ifndef LE_LIST_MINB
 #define LE_LIST_MINB 4
 #endif
+constexpr int kListUnroll = LE_LIST_UNROLL;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -1280,132 +1285,90 @@ __global__ void k_tables(Geom g, Dyn *__restrict__ d) {
 }
 
 // ------------------------------------------------------------- rebuild: list
-// LE-aware Verlet list from the build positions, one warp per 32 consecutive
-// cell-sorted particles: the same 32 particles whose list rows the pair
-// kernel streams (entry k of lane l is row k, column l of the warp's tile).
-//
-// The warp's particles sit in a few consecutive cells, usually of one cell
-// row (cy, cz).  For each group of lanes that share a home row, the union of
-// their neighbour cells in a neighbour row (dcy, dcz) is one range of x cells:
-// xa - 1 .. xb + 1 for a row inside the box, and for a row across the
-// top/bottom face the window shifted by the image offset at the build (m_b
-// cells plus f_b; 3 or 4 cells per home cell).  The candidates of that range
-// are staged 32 at a time in shared memory -- coalesced loads, each moved into
-// the group's frame by the lane that loads it -- and every lane of the group
-// tests every staged candidate from the broadcast copy.  A candidate within
-// the list radius is stored with the slot of its image as seen from the
-// lane's own cell.  Rows that no lane of the group reaches are skipped.
+// LE-aware Verlet list from the build positions.  Neighbour cells of cell
+// (cx,cy,cz): for a y/z neighbour row inside the box, the x cells cx-1..cx+1;
+// for a row across the top/bottom face, the x window shifted by the image
+// offset: 3 or 4 cells covering every cell within rl of the shifted row
+// (f_build/lx decides whether the window reaches a 4th cell).  Rows and
+// cells whose box lies farther than rl from the particle are skipped.
 template <class R, class BX>
 __device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                              Bufs<R> s1, Work w, int target_cur, BX bx) {
-  __shared__ float4 s_cand[kListMaxThreads / 32][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float s_offx[kNumSlots];
+  for (int e = threadIdx.x; e < kNumSlots; e += blockDim.x) s_offx[e] = (float)d->off_build[e][0];
+  __syncthreads();
   const int tgt = target_cur ? d->cur : 1 - d->cur;
   const Bufs<R> b = pick(tgt, s0, s1);
   const int i = bx() * blockDim.x + threadIdx.x;
-  const bool active = i < g.n;
-  const float4 qi = active ? b.pb[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  int cx = 0, cy = 0, cz = 0;
-  if (active) cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
-  const int nc0 = g.nc[0], nc1 = g.nc[1], nc2 = g.nc[2];
-  const float lx = (float)g.lc[0], ly = (float)g.lc[1], lz = (float)g.lc[2];
-  const float rl2 = g.rl2_build;
-  const float hy = g.half_lc_f[1], hz = g.half_lc_f[2];
-  const int mb = d->m_build;
-  const float fb = (float)d->f_build;
-  const int maxnb = g.maxnb;
-  uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)maxnb * 32u + lane;
-  const uint32_t self = make_entry(i, slot_code(0, 0, 0, 0));
   int cnt = 0;
-  const int row_i = active ? cy + nc1 * cz : -1;
-  unsigned pending = __ballot_sync(0xffffffffu, active);
-  while (pending) {
-    const int row0 = __shfl_sync(0xffffffffu, row_i, __ffs(pending) - 1);
-    const bool mine = row_i == row0;
-    pending &= ~__ballot_sync(0xffffffffu, mine);
-    const int xa = __reduce_min_sync(0xffffffffu, mine ? cx : 0x7fffffff);
-    const int xb = __reduce_max_sync(0xffffffffu, mine ? cx : -0x7fffffff);
-    const int gcy = row0 % nc1, gcz = row0 / nc1;
-    // the lane's position in the frame of the group's first cell, and its
-    // cell offset from that cell (added to a staged entry, it gives the slot)
-    const float xi = fmaf((float)(cx - xa), lx, qi.x);
-    const uint32_t kbase = (uint32_t)(cx - xa);
+  if (i < g.n) {
+    const float4 qi = b.pb[i];
+    int cx, cy, cz;
+    cell_coords(g, __float_as_int(qi.w), cx, cy, cz);
+    const float rl2 = g.rl2_build;
+    const float hx = g.half_lc_f[0], hy = g.half_lc_f[1], hz = g.half_lc_f[2];
+    const float ly = (float)g.lc[1], lz = (float)g.lc[2];
+    const int mb = d->m_build;
+    uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
     for (int dcz = -1; dcz <= 1; ++dcz) {
-      const float gz = fmaxf(fabsf(qi.z + (float)dcz * lz) - hz, 0.f);
-      if (!__any_sync(0xffffffffu, mine && gz * gz < rl2)) continue;
-      int czj = gcz - dcz, cross = 0;
-      if (czj < 0) { czj += nc2; cross = 1; }
-      else if (czj >= nc2) { czj -= nc2; cross = 1; }
+      const float az = qi.z + (float)dcz * lz;
+      const float gz = fmaxf(fabsf(az) - hz, 0.f);
+      if (gz * gz >= rl2) continue;
+      int czj = cz - dcz, cross = 0;
+      if (czj < 0) { czj += g.nc[2]; cross = 1; }
+      else if (czj >= g.nc[2]) { czj -= g.nc[2]; cross = 1; }
       int kmin = -1, kmax = 1;
       if (cross) {
         kmin = d->win_lo[dcz > 0 ? 1 : 0];
         kmax = d->win_hi[dcz > 0 ? 1 : 0];
       }
-      const int sh = cross ? dcz * mb : 0;           // whole cells of the image offset
-      const float xsh = cross ? (float)dcz * fb : 0.f; // its remainder
-      const float zoff = (float)dcz * lz;
       for (int dcy = -1; dcy <= 1; ++dcy) {
-        const float gy = fmaxf(fabsf(qi.y + (float)dcy * ly) - hy, 0.f);
-        if (!__any_sync(0xffffffffu, mine && gy * gy + gz * gz < rl2)) continue;
-        const int cyj = wrap_index(gcy - dcy, nc1);
-        const int base = nc0 * (cyj + nc1 * czj);
-        const float yoff = (float)dcy * ly;
-        // slot fields of this row, the x field's bias 3 included
-        const uint32_t fields = (uint32_t)slot_code(0, dcy, dcz, cross);
-        // candidate x cells, unwrapped: a home cell cx takes cx - k + sh for
-        // k in [kmin, kmax]; taken in runs that do not cross the periodic x face
-        int u = xa - kmax + sh;
-        const int uend = xb - kmin + sh;
-        while (u <= uend) {
-          const int c0 = wrap_index(u, nc0);
-          const int len = min(uend - u + 1, nc0 - c0);
-          // a candidate in x cell cxj of this run sits m = cxj + mshift cells
-          // from the group's first cell in the image frame: k = (cx - xa) - m
-          const int mshift = u - c0 - sh - xa;
+        const float ay = qi.y + (float)dcy * ly;
+        const float gy = fmaxf(fabsf(ay) - hy, 0.f);
+        const float gyz = gy * gy + gz * gz;
+        if (gyz >= rl2) continue;
+        const int cyj = wrap_index(cy - dcy, g.nc[1]);
+        const int rowbase = g.nc[0] * (cyj + g.nc[1] * czj);
+        for (int k = kmin; k <= kmax; ++k) {
+          const int slot = slot_code(k, dcy, dcz, cross);
+          const float ax = qi.x + s_offx[slot];
+          const float gx = fmaxf(fabsf(ax) - hx, 0.f);
+          if (gx * gx + gyz >= rl2) continue;
+          const int cxj = wrap_index(cx - k + (cross ? dcz * mb : 0), g.nc[0]);
+          const int cj = rowbase + cxj;
           // clamped so that a corrupt range can never leave the particle arrays
-          const int j0 = min(max(w.cell_start[base + c0], 0), g.n);
-          const int j1 = min(max(w.cell_start[base + c0 + len], j0), g.n);
-          for (int jb = j0; jb < j1; jb += 32) {
-            const int jj = jb + lane;
-            if (jj < j1) {
-              const float4 q = __ldg(b.pb + jj);
-              const int m = (__float_as_int(q.w) - base) + mshift;
-              // the entry for a lane in the group's first cell (k = -m); a
-              // lane adds its own cell offset
-              const uint32_t e0 = make_entry(jj, 0) + fields - (uint32_t)m;
-              s_cand[warp][lane] = make_float4(fmaf((float)m, lx, q.x) - xsh, q.y - yoff,
-                                               q.z - zoff, __uint_as_float(e0));
+          const int j0 = min(max(w.cell_start[cj], 0), g.n);
+          const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
+          const bool self_slot = (slot == slot_code(0, 0, 0, 0));
+          const uint32_t tag = (uint32_t)slot;
+          int j = j0;
+          auto emit = [&](int jj, const float4 &q) {
+            const float dx = ax - q.x, dy = ay - q.y, dz = az - q.z;
+            if (dx * dx + dy * dy + dz * dz < rl2 && !(self_slot && jj == i)) {
+              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = ((uint32_t)jj << kSlotBits) | tag;
+              ++cnt;
             }
-            __syncwarp();
-            const int nj = min(32, j1 - jb);
-            if (mine) {
-#pragma unroll 4
-              for (int c = 0; c < nj; ++c) {
-                const float4 cq = s_cand[warp][c];
-                const float dx = xi - cq.x, dy = qi.y - cq.y, dz = qi.z - cq.z;
-                const uint32_t e = __float_as_uint(cq.w) + kbase;
-                if (dx * dx + dy * dy + dz * dz < rl2 && e != self) {
-                  out[min(cnt, maxnb - 1) * 32] = e;
-                  ++cnt;
-                }
-              }
-            }
-            __syncwarp();
+          };
+          // kListUnroll candidates per pass: their loads are in flight together
+          for (; j + kListUnroll <= j1; j += kListUnroll) {
+            float4 q[kListUnroll];
+#pragma unroll
+            for (int u = 0; u < kListUnroll; ++u) q[u] = __ldg(b.pb + j + u);
+#pragma unroll
+            for (int u = 0; u < kListUnroll; ++u) emit(j + u, q[u]);
           }
-          u += len;
+          for (; j < j1; ++j) emit(j, __ldg(b.pb + j));
         }
       }
     }
-  }
-  if (active) {
     w.ncount[i] = cnt;
     atomicMax(&d->list_max, cnt);
-    if (cnt > maxnb) atomicOr(&d->err, (int)kErrCapacity);
+    if (cnt > g.maxnb) atomicOr(&d->err, (int)kErrCapacity);
   }
   // total list entries (for the mean list length), one atomic per block
   __shared__ unsigned long long s_tot[kListMaxThreads / 32];
   const unsigned long long c = warp_sum((unsigned long long)cnt);
-  if (lane == 0) s_tot[warp] = c;
+  if ((threadIdx.x & 31) == 0) s_tot[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
