@@ -1310,6 +1310,7 @@ __device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, 
     const float ly = (float)g.lc[1], lz = (float)g.lc[2];
     const int mb = d->m_build;
     uint32_t *out = w.nbr + (size_t)(i >> 5) * (size_t)g.maxnb * 32u + (i & 31);
+    const int cap = g.maxnb - 1;
     for (int dcz = -1; dcz <= 1; ++dcz) {
       const float az = qi.z + (float)dcz * lz;
       const float gz = fmaxf(fabsf(az) - hz, 0.f);
@@ -1339,13 +1340,16 @@ __device__ __forceinline__ void rb_list_body(const Geom g, Dyn *__restrict__ d, 
           // clamped so that a corrupt range can never leave the particle arrays
           const int j0 = min(max(w.cell_start[cj], 0), g.n);
           const int j1 = min(max(w.cell_start[cj + 1], j0), g.n);
-          const bool self_slot = (slot == slot_code(0, 0, 0, 0));
+          // the particle itself is a candidate only in its own cell's slot
+          const int self_j = slot == slot_code(0, 0, 0, 0) ? i : -1;
           const uint32_t tag = (uint32_t)slot;
           int j = j0;
           auto emit = [&](int jj, const float4 &q) {
             const float dx = ax - q.x, dy = ay - q.y, dz = az - q.z;
-            if (dx * dx + dy * dy + dz * dz < rl2 && !(self_slot && jj == i)) {
-              if (cnt < g.maxnb) out[(size_t)cnt * 32u] = ((uint32_t)jj << kSlotBits) | tag;
+            if (dx * dx + dy * dy + dz * dz < rl2 && jj != self_j) {
+              // past the capacity the last row is overwritten (the overflow is
+              // reported and the list regrown)
+              out[min(cnt, cap) * 32] = ((uint32_t)jj << kSlotBits) | tag;
               ++cnt;
             }
           };
