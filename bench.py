@@ -276,10 +276,15 @@ def force_kernel_bytes(n: int, mean_nb: float) -> float:
     return n * (16 + 4 + 4 * mean_nb + 16)
 
 
-def force_launch_bytes(n: int, mean_nb: float) -> float:
+def force_launch_bytes(n: int, mean_nb: float, fused_drift: bool = False) -> float:
     """The same launch's bytes with its fused epilogue (Langevin, second half
     kick, samples): + half-step velocity 16 + particle id 4 read, total force
-    16 and velocity 16 written."""
+    16 and velocity 16 written.  Fused with the next step's kick and drift
+    (FP32 inside a multi-step call), no force is written and the launch also
+    reads p, its low part and the build position (48) and writes p, the low
+    part and the next fixed-point copy (48)."""
+    if fused_drift:
+        return n * (16 + 4 + 4 * mean_nb) + n * (16 + 4 + 16) + n * (48 + 48)
     return force_kernel_bytes(n, mean_nb) + n * (16 + 4 + 16 + 16)
 
 
@@ -372,14 +377,17 @@ def run_ours(args):
     rebuilds = c1["rebuilds"] - c0["rebuilds"]
     ncell = c1["cells"][0] * c1["cells"][1] * c1["cells"][2]
     passes = math.ceil(max(1, math.ceil(math.log2(max(2, ncell)))) / 9)
-    # per step: drift, decide, force; per rebuild: bin, 5 per sort pass
-    # (counts, 3 scan kernels, scatter), permute, ranges, list, finish
-    launches = 3 * args.steps + rebuilds * (1 + 5 * passes + 4)
+    # per step: decide, force, and a drift launch in the first step only (the
+    # force launch of every other step ran its drift: FP32 without DPD); per
+    # rebuild: bin, 5 per sort pass (counts, 3 scan kernels, scatter),
+    # permute, ranges, list, finish
+    fused = True  # this box runs FP32 with the Langevin thermostat
+    launches = (2 * args.steps + 1 if fused else 3 * args.steps) + rebuilds * (1 + 5 * passes + 4)
     mean_nb = c1["list_mean"]
     kbytes = force_kernel_bytes(w.n, mean_nb)
     f_avg_s = force_ms / args.steps * 1e-3
     achieved = kbytes / f_avg_s / 1e9
-    achieved_fused = force_launch_bytes(w.n, mean_nb) / f_avg_s / 1e9
+    achieved_fused = force_launch_bytes(w.n, mean_nb, fused_drift=fused) / f_avg_s / 1e9
     peak, peak_kind = measured_peak()
     traffic_pp = profiled_traffic(os.path.join(ROOT, "paper_2109_11083_gb300", "csrc",
                                                "le_kernels.cu"))
@@ -443,10 +451,17 @@ def run_ours(args):
                                           if tuned else None)),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "kernel": "k_force (pair force + Langevin + kick + samples)",
+                         "kernel": ("k_force (pair force + Langevin + kick + samples"
+                                    + (", + the next step's kick and drift in all but the "
+                                       "last step)" if fused else ")")),
                          "algorithmic_bytes_per_launch": kbytes,
                          "bytes_count": "pair force alone: (16 + 4 + 4 n_list + 16) B per particle",
                          "achieved_with_fused_epilogue": achieved_fused,
+                         "fused_bytes_count": ("(152 + 4 n_list) B per particle: the pair force "
+                                               "without the force write, the epilogue and the "
+                                               "next drift" if fused else
+                                               "(88 + 4 n_list) B per particle: the pair force "
+                                               "and the epilogue"),
                          "avg_launch_ms": f_avg_s * 1e3,
                          "traffic": (traffic_pp * w.n if traffic_pp else None)},
             "kernel_ms_per_step": {"k_force": force_ms / args.steps,

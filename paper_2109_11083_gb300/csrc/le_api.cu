@@ -28,7 +28,7 @@ using namespace le;
 namespace {
 constexpr int kChunk = 16;
 constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
-constexpr int kStateVersion = 4;
+constexpr int kStateVersion = 5;
 }  // namespace
 
 struct le_sim {
@@ -209,20 +209,21 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
     void *p, *plo, *v, *ft, *fc;
     float4 *pb;
     int *gid;
-    int4 *q = nullptr;
+    int4 *q = nullptr, *q2 = nullptr;
     CKS(dalloc(s, (char **)&p, n * vb));
     plo = nullptr;
     if (prec == 1) CKS(dalloc(s, (char **)&plo, n * sizeof(float4)));
     if (prec == 1) CKS(dalloc(s, &q, n));
+    if (prec == 1) CKS(dalloc(s, &q2, n));
     CKS(dalloc(s, (char **)&v, n * vb));
     CKS(dalloc(s, (char **)&ft, n * vb));
     CKS(dalloc(s, (char **)&fc, n * vb));
     CKS(dalloc(s, &pb, n));
     CKS(dalloc(s, &gid, n));
     if (prec == 1) {
-      s->s.f32[k] = Bufs<float>{(float4 *)p, (float4 *)plo, (float4 *)v, (float4 *)ft, (float4 *)fc, pb, gid, q};
+      s->s.f32[k] = Bufs<float>{(float4 *)p, (float4 *)plo, (float4 *)v, (float4 *)ft, (float4 *)fc, pb, gid, q, q2};
     } else {
-      s->s.f64[k] = Bufs<double>{(D4 *)p, (float4 *)plo, (D4 *)v, (D4 *)ft, (D4 *)fc, pb, gid, nullptr};
+      s->s.f64[k] = Bufs<double>{(D4 *)p, (float4 *)plo, (D4 *)v, (D4 *)ft, (D4 *)fc, pb, gid, nullptr, nullptr};
     }
   }
   Work &w = s->s.w;
@@ -355,16 +356,19 @@ void fill_geom(le_sim *s, const double box[3], double shear_rate, double rc, dou
 // ------------------------------------------------------------- graph capture
 // Records `steps` steps of system s on stream st, which must already be
 // capturing into `graph`: drift, decide (sets the IF condition), IF(rebuild),
-// force.  Used for a handle's own graphs and for the branches of a batch.
+// force.  Where the system allows it, the force launch of every step but the
+// last also runs the next step's drift (mode 2), so only the first step has a
+// drift launch of its own.
 cudaError_t record_steps(le_sim *s, cudaStream_t st, cudaGraph_t graph, int steps,
                          std::vector<cudaEvent_t> *ev) {
   cudaError_t ce = cudaSuccess;
+  const bool fuse = can_fuse_drift(s->s);
   for (int k = 0; k < steps && ce == cudaSuccess; ++k) {
     cudaGraphConditionalHandle handle;
     ce = cudaGraphConditionalHandleCreate(&handle, graph, 0, 0);
     if (ce != cudaSuccess) break;
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 0], st, cudaEventRecordExternal);
-    launch_drift(s->s, st);
+    if (k == 0 || !fuse) launch_drift(s->s, st);
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 1], st, cudaEventRecordExternal);
     launch_decide(s->s, handle, 1, st);
     const cudaGraphNode_t *deps = nullptr;
@@ -391,7 +395,7 @@ cudaError_t record_steps(le_sim *s, cudaStream_t st, cudaGraph_t graph, int step
     ce = cudaStreamEndCapture(s->cap_side, &body);
     if (ce != cudaSuccess) break;
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 2], st, cudaEventRecordExternal);
-    launch_force(s->s, 0, st);
+    launch_force(s->s, fuse && k + 1 < steps ? 2 : 0, st);
     if (ev) cudaEventRecordWithFlags((*ev)[4 * k + 3], st, cudaEventRecordExternal);
   }
   return ce;
@@ -661,10 +665,13 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
   return fail(s, LE_ERR_CAPACITY, "neighbour list could not be sized");
 }
 
-// One step without graphs: the host reads the rebuild decision back.
-static le_status eager_step(le_sim *s, cudaEvent_t *ev) {
+// One step without graphs: the host reads the rebuild decision back.  The
+// same launches as a graph of the call's steps: `drift` is false where the
+// previous step's force launch ran this step's drift, `fuse` (mode 2) hands
+// the next step's drift to this force launch.
+static le_status eager_step(le_sim *s, cudaEvent_t *ev, bool drift, bool fuse) {
   if (ev) CK(cudaEventRecord(ev[0], s->stream));
-  launch_drift(s->s, s->stream);
+  if (drift) launch_drift(s->s, s->stream);
   if (ev) CK(cudaEventRecord(ev[1], s->stream));
   launch_decide(s->s, 0, 0, s->stream);
   CK(cudaMemcpyAsync(s->h_scalar, &s->s.dyn->rebuild, sizeof(int), cudaMemcpyDeviceToHost,
@@ -672,15 +679,21 @@ static le_status eager_step(le_sim *s, cudaEvent_t *ev) {
   CKS(sync(s));
   if (*(int *)s->h_scalar) launch_rebuild(s->s, false, s->stream);
   if (ev) CK(cudaEventRecord(ev[2], s->stream));
-  launch_force(s->s, 0, s->stream);
+  launch_force(s->s, fuse ? 2 : 0, s->stream);
   if (ev) CK(cudaEventRecord(ev[3], s->stream));
   CK(cudaGetLastError());
   return LE_OK;
 }
 
+// eager_step k of a call of n steps, fused as a graph of n steps would be
+static le_status eager_step_of(le_sim *s, cudaEvent_t *ev, int64_t k, int64_t n) {
+  const bool f = can_fuse_drift(s->s);
+  return eager_step(s, ev, k == 0 || !f, f && k + 1 < n);
+}
+
 static le_status step_once(le_sim *s, int64_t nsteps) {
   if (s->eager) {
-    for (int64_t k = 0; k < nsteps; ++k) CKS(eager_step(s, nullptr));
+    for (int64_t k = 0; k < nsteps; ++k) CKS(eager_step_of(s, nullptr, k, nsteps));
     launch_fold(s->s, s->stream);
     CK(cudaGetLastError());
     return read_dyn(s);
@@ -760,7 +773,7 @@ LE_API le_status le_step_profiled(le_sim *s, int64_t nsteps, double *force_ms, d
   le_status st = LE_OK;
   if (s->eager) {
     CK(cudaEventRecord(t0, s->stream));
-    for (int64_t k = 0; k < nsteps && st == LE_OK; ++k) st = eager_step(s, &ev[4 * k]);
+    for (int64_t k = 0; k < nsteps && st == LE_OK; ++k) st = eager_step_of(s, &ev[4 * k], k, nsteps);
     CK(cudaEventRecord(t1, s->stream));
     launch_fold(s->s, s->stream);
     if (st == LE_OK) st = read_dyn(s);

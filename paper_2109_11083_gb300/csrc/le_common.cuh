@@ -164,6 +164,8 @@ struct Dyn {
   int m_build;
   int win_lo[2], win_hi[2];  // x-cell window of rows across the top/bottom face, [dcz=-1, dcz=+1]
   int cur;               // buffer set holding the current state
+  int qpar;              // 1: the current fixed-point copy is q2 (FP32)
+  int qflip;             // set by a fused pair+drift launch: swap q and q2 at the next decision
   unsigned maxdisp2;     // float bits of the largest squared peculiar displacement since the build
   int rebuild;           // 1 if this step rebuilt the lists
   int err;               // ErrBits
@@ -197,6 +199,7 @@ template <class R> struct Bufs {
   float4 *pb;              // p at the last build (x,y,z); w = build cell id (int bits)
   int *gid;                // caller's particle id
   int4 *q;                 // FP32 mode: p in fixed point (x,y,z); w = bits of p.w (float)
+  int4 *q2;                // FP32 mode: second fixed-point copy (Dyn::qpar names the current one)
 };
 
 // Shared (not double-buffered) work arrays of one system.
@@ -229,7 +232,21 @@ __device__ __forceinline__ Bufs<R> pick(int cur, const Bufs<R> &a, const Bufs<R>
   r.pb = cur ? b.pb : a.pb;
   r.gid = cur ? b.gid : a.gid;
   r.q = cur ? b.q : a.q;
+  r.q2 = cur ? b.q2 : a.q2;
   return r;
+}
+
+// The buffer set with q naming the fixed-point copy of the current positions
+// and q2 the other one (a pair kernel fused with the next drift reads q and
+// writes the drifted copy to q2; the next step decision swaps them).
+template <class R>
+__device__ __forceinline__ Bufs<R> with_cur_q(Bufs<R> b, int qpar) {
+  if (qpar) {
+    int4 *t = b.q;
+    b.q = b.q2;
+    b.q2 = t;
+  }
+  return b;
 }
 
 // Image offset of Eq. 4 at integer step n, in [0, Lx).

@@ -12,6 +12,10 @@
 //             minimum image; Ftot = Fc - xi m (v - v_s e_x) + random (Eq. 5);
 //             v += dt/2m Ftot; Eq. 15 xz stress, peculiar temperature and the
 //             vx(z) profile as fixed-point integer sums.
+// Inside a multi-step graph (FP32 without DPD) k_force of step n also runs the
+// k_drift of step n+1 for its own particle (mode 2): neighbours are read only
+// through the fixed-point copy q, so the drifted copy goes to a second array
+// q2, and k_decide swaps the two.  Same arithmetic, same results.
 #include <cuda_runtime.h>
 
 #include "le_common.cuh"
@@ -142,59 +146,75 @@ struct VBlock {
 };
 
 // ------------------------------------------------------------------ k_drift
+// First half kick of particle i with the total force f, drift, and (FP32) the
+// fixed-point copy of the new position written to qout[i].  Returns the
+// squared peculiar displacement since the build: the streaming
+// shear*tau*(z_b - Lz/2) along x (z_b = build-time z = reference + build
+// displacement) is shared by neighbours and does not use up the skin.
 template <class R>
-__device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                           Bufs<R> s1, int bx) {
-  const Bufs<R> b = pick(d->cur, s0, s1);
-  const int i = bx * blockDim.x + threadIdx.x;
-  // time since the build at the step this drift produces
-  const float shear_tau = g.cf.shear * (float)(d->step + 1 - d->build_step) * g.cf.dt;
-  float disp2 = 0.f;
-  if (i < g.n) {
-    const R half = kc<R>(g).half_dt_m;
-    const R dt = kc<R>(g).dt;
-    V4<R> v = b.v[i];
-    const V4<R> f = b.ft[i];
-    v.x += half * f.x;
-    v.y += half * f.y;
-    v.z += half * f.z;
-    V4<R> p = b.p[i];
-    if constexpr (sizeof(R) == 4) {
-      float4 lo = b.plo[i];
-      two_sum_acc(p.x, lo.x, dt * v.x);
-      two_sum_acc(p.y, lo.y, dt * v.y);
-      two_sum_acc(p.z, lo.z, dt * v.z);
-      b.plo[i] = lo;
-      // a displacement beyond the fixed-point range is reported (LE_ERR_RANGE)
-      if (!(fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))) < g.qmax))
-        atomicOr(&d->err, (int)kErrRange);
-      b.q[i] = quantize(g, p, lo);
-    } else {
-      p.x += dt * v.x;
-      p.y += dt * v.y;
-      p.z += dt * v.z;
-    }
-    b.v[i] = v;
-    b.p[i] = p;
-    // peculiar displacement since the build: the streaming shear*tau*(z_b -
-    // Lz/2) along x (z_b = build-time z = reference + build displacement) is
-    // shared by neighbours and does not use up the skin
-    const float4 q = b.pb[i];
-    const float zb = (float)p.w + q.z;
-    const float dx = (float)p.x - q.x - shear_tau * (zb - (float)kc<R>(g).half_Lz);
-    const float dy = (float)p.y - q.y, dz = (float)p.z - q.z;
-    disp2 = dx * dx + dy * dy + dz * dz;
+__device__ __forceinline__ float kick_drift(const Geom &g, Dyn *__restrict__ d, const Bufs<R> &b,
+                                            int4 *qout, int i, V4<R> v, const V4<R> &f,
+                                            float shear_tau) {
+  const R half = kc<R>(g).half_dt_m;
+  const R dt = kc<R>(g).dt;
+  v.x += half * f.x;
+  v.y += half * f.y;
+  v.z += half * f.z;
+  V4<R> p = b.p[i];
+  if constexpr (sizeof(R) == 4) {
+    float4 lo = b.plo[i];
+    two_sum_acc(p.x, lo.x, dt * v.x);
+    two_sum_acc(p.y, lo.y, dt * v.y);
+    two_sum_acc(p.z, lo.z, dt * v.z);
+    b.plo[i] = lo;
+    // a displacement beyond the fixed-point range is reported (LE_ERR_RANGE)
+    if (!(fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))) < g.qmax))
+      atomicOr(&d->err, (int)kErrRange);
+    qout[i] = quantize(g, p, lo);
+  } else {
+    p.x += dt * v.x;
+    p.y += dt * v.y;
+    p.z += dt * v.z;
   }
+  b.v[i] = v;
+  b.p[i] = p;
+  const float4 q = b.pb[i];
+  const float zb = (float)p.w + q.z;
+  const float dx = (float)p.x - q.x - shear_tau * (zb - (float)kc<R>(g).half_Lz);
+  const float dy = (float)p.y - q.y, dz = (float)p.z - q.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// Largest value of v over the block, folded into d->maxdisp2 (one atomic per
+// block; all threads of the block call it).
+template <int NWARPS>
+__device__ __forceinline__ void block_max_disp(Dyn *__restrict__ d, float v) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) disp2 = fmaxf(disp2, __shfl_xor_sync(0xffffffffu, disp2, o));
-  __shared__ float sm[kDriftThreads / 32];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = disp2;
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ float sm[NWARPS];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     float m = sm[0];
-    for (int w = 1; w < kDriftThreads / 32; ++w) m = fmaxf(m, sm[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
     if (m > 0.f) atomicMax(&d->maxdisp2, __float_as_uint(m));
   }
+}
+
+// time since the build at the step a drift from the current step produces
+__device__ __forceinline__ float drift_shear_tau(const Geom &g, const Dyn *__restrict__ d) {
+  return g.cf.shear * (float)(d->step + 1 - d->build_step) * g.cf.dt;
+}
+
+template <class R>
+__device__ __forceinline__ void drift_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                           Bufs<R> s1, int bx) {
+  const Bufs<R> b = with_cur_q(pick(d->cur, s0, s1), d->qpar);
+  const int i = bx * blockDim.x + threadIdx.x;
+  const float shear_tau = drift_shear_tau(g, d);
+  float disp2 = 0.f;
+  if (i < g.n) disp2 = kick_drift<R>(g, d, b, b.q, i, b.v[i], b.ft[i], shear_tau);
+  block_max_disp<kDriftThreads / 32>(d, disp2);
 }
 template <class R>
 __global__ void __launch_bounds__(kDriftThreads) k_drift(const __grid_constant__ Geom g,
@@ -246,6 +266,11 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
   }
   __syncthreads();
   if (t == 0) {
+    // a pair kernel fused with the drift wrote the new positions to q2
+    if (d->qflip) {
+      d->qpar ^= 1;
+      d->qflip = 0;
+    }
     if (pending) {
       const double V = g.L[0] * g.L[1] * g.L[2];
       d->sum_sxz += -(double)d->acc_sxz * kInvFix / V;
@@ -638,7 +663,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   G.ly = R(g.lc[1]);
   G.lz = R(g.lc[2]);
   G.s = R(d->s);
-  const bool sample = mode == 0 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
+  const bool sample = mode != 1 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
   if (sample)
     for (int b = t; b < 3 * g.nbins; b += blockDim.x) s_prof[b] = 0;
   if (lane == 0) {
@@ -648,7 +673,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   mbar_init_fence();
   __syncthreads();
 
-  const Bufs<R> b = pick(cur, s0, s1);
+  const Bufs<R> b = with_cur_q(pick(cur, s0, s1), d->qpar);
   const KConst<R> &K = kc<R>(g);
   const int i = bx() * blockDim.x + t;
   const bool active = i < g.n;
@@ -806,6 +831,7 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
     }
   };
   R sxz = R(0), ke = R(0);
+  float disp2 = 0.f;  // mode 2: squared peculiar displacement after the drift
   int bin = -1;
   R vxw = R(0), vy2 = R(0);
   if (active) {
@@ -915,18 +941,22 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       ftz += -xm * v.z + amp * u[2];
     }
     V4<R> nv = v;
-    if (mode == 0) {
+    if (mode != 1) {
       const R half = K.half_dt_m;
       nv.x = v.x + half * ftx;
       nv.y = v.y + half * fty;
       nv.z = v.z + half * ftz;
     }
-    b.fc[i] = make4<R>(fx, fy, fz, R(0));
-    b.ft[i] = make4<R>(ftx, fty, ftz, R(0));
+    // fused with the next drift (mode 2), the total force goes straight into
+    // the next half kick and neither force is stored
+    if (mode != 2) {
+      b.fc[i] = make4<R>(fx, fy, fz, R(0));
+      b.ft[i] = make4<R>(ftx, fty, ftz, R(0));
+    }
     // DPD reads the other particles' half-step velocities: the kicked ones go
     // to a scratch array, copied back once every thread has read
     if constexpr (DPD) reinterpret_cast<V4<R> *>(w.vnew)[i] = nv;
-    else b.v[i] = nv;
+    else if (mode != 2) b.v[i] = nv;
     if (!isfinite(ftx + fty + ftz) || !isfinite(nv.x + nv.y + nv.z))
       atomicOr(&d->err, (int)kErrNonfinite);
     if (sample) {
@@ -948,6 +978,20 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       bin = bb < 0 ? 0 : (bb >= g.nbins ? g.nbins - 1 : bb);
       vxw = vw;
       vy2 = m * nv.y * nv.y;  // T_y profile (Sec. 3.1)
+    }
+    // mode 2: the next step's first half kick and drift (FP32 without DPD,
+    // where neighbours are read only through the fixed-point copy q; the
+    // drifted copy goes to q2)
+    if constexpr (sizeof(R) == 4 && !DPD) {
+      if (mode == 2)
+        disp2 = kick_drift<R>(g, d, b, b.q2, i, nv, make4<R>(ftx, fty, ftz, R(0)),
+                              drift_shear_tau(g, d));
+    }
+  }
+  if constexpr (sizeof(R) == 4 && !DPD) {
+    if (mode == 2) {
+      block_max_disp<kForceWarps>(d, disp2);
+      if (t == 0 && bx() == 0) d->qflip = 1;
     }
   }
   if (!sample) return;
@@ -1182,7 +1226,7 @@ __device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ 
                                                 const uint32_t *__restrict__ sval, int bx) {
   const int cur = d->cur;
   const Bufs<R> src = pick(cur, s0, s1);
-  const Bufs<R> dst = pick(1 - cur, s0, s1);
+  const Bufs<R> dst = with_cur_q(pick(1 - cur, s0, s1), d->qpar);
   const int k = bx * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const int o = min((int)sval[k], g.n - 1);
@@ -1248,7 +1292,7 @@ __global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom 
 // positions and ranks from the stored build record of the current set.
 template <class R>
 __global__ void k_relist_prep(Geom g, Dyn *__restrict__ d, Bufs<R> s0, Bufs<R> s1, Work w) {
-  const Bufs<R> b = pick(d->cur, s0, s1);
+  const Bufs<R> b = with_cur_q(pick(d->cur, s0, s1), d->qpar);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= g.n) return;
   const float4 q = b.pb[k];
@@ -1767,6 +1811,8 @@ void launch_decide(const SysDev &s, cudaGraphConditionalHandle h, int use_cond, 
 }
 
 void launch_fold(const SysDev &s, cudaStream_t st) { k_fold<<<1, 256, 0, st>>>(s.g, s.dyn, s.w); }
+
+bool can_fuse_drift(const SysDev &s) { return s.prec == 1 && s.g.thermostat != 3; }
 
 void launch_force(const SysDev &s, int mode, cudaStream_t st) {
   const int nb = blocks_for(s.g.n, s.force_threads);

@@ -68,8 +68,12 @@ void launch_rebuild(const SysDev &s, bool from_import, cudaStream_t st);
 // current set from its stored build record (checkpoint restore, rollback).
 void launch_relist(const SysDev &s, cudaStream_t st);
 // mode 0: a normal step (forces, thermostat, second half kick, samples);
-// mode 1: initial forces only (velocity unchanged, no samples).
+// mode 1: initial forces only (velocity unchanged, no samples);
+// mode 2: mode 0 followed by the next step's kick and drift of each particle
+//         (FP32 without DPD only: can_fuse_drift), forces not stored.
 void launch_force(const SysDev &s, int mode, cudaStream_t st);
+// whether launch_force may run mode 2 for this system
+bool can_fuse_drift(const SysDev &s);
 void launch_fold(const SysDev &s, cudaStream_t st);
 void launch_import(const SysDev &s, cudaStream_t st);     // reads stage[0:3n] pos, [3n:6n] vel
 void launch_export(const SysDev &s, cudaStream_t st);     // writes stage: pos, vel; and fc into partial-free area

@@ -226,6 +226,7 @@ template <class R> void carve_set(Carver &cv, Bufs<R> &b, int64_t n, bool lo) {
   b.pb = cv.take<float4>(n);
   b.gid = cv.take<int>(n);
   b.q = lo ? cv.take<int4>(n) : nullptr;
+  b.q2 = nullptr;  // no fused drift here
 }
 
 // Lays every buffer of a one-shot force evaluation out in the static array.
