@@ -1239,8 +1239,11 @@ le_status batch_capture(le_batch *b, int steps, cudaGraphExec_t *out) {
   }
   cudaError_t ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, cudaGetErrorString(ce));
+  // as for one system: where a group allows it, each force launch but the
+  // last also runs the next step's drift
   for (int k = 0; k < steps; ++k)
-    for (const BatchGroup &gr : b->groups) launch_batch_step(gr.grid, b->cap);
+    for (const BatchGroup &gr : b->groups)
+      launch_batch_step(gr.grid, b->cap, k == 0, k + 1 < steps);
   cudaGraph_t captured = nullptr;
   cudaError_t ee = cudaStreamEndCapture(b->cap, &captured);
   if (ce == cudaSuccess) ce = ee;

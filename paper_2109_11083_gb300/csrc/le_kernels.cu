@@ -39,6 +39,19 @@ template <class R> __device__ __forceinline__ V4<R> make4(R x, R y, R z, R w) {
   return v;
 }
 
+// Rounded operations that the compiler may not contract into FMAs: the DPD
+// pair arithmetic and the thermostat's streaming velocity are written
+// with them so that every kernel that inlines them (a system's own step, a
+// batch launch) computes the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // hi + lo += a with the rounding error of the sum kept in lo (TwoSum followed
 // by a renormalisation): ~48 significant bits for the displacement.
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float a) {
@@ -157,9 +170,13 @@ __device__ __forceinline__ float kick_drift(const Geom &g, Dyn *__restrict__ d, 
                                             float shear_tau) {
   const R half = kc<R>(g).half_dt_m;
   const R dt = kc<R>(g).dt;
-  v.x += half * f.x;
-  v.y += half * f.y;
-  v.z += half * f.z;
+  // explicit fma (and explicitly rounded products below) wherever a product
+  // meets a sum: every kernel that inlines this code (a system's own step, a
+  // batch launch, fused with the pair kernel or not) then rounds alike, and
+  // their results stay bit-identical
+  v.x = fma(half, f.x, v.x);
+  v.y = fma(half, f.y, v.y);
+  v.z = fma(half, f.z, v.z);
   V4<R> p = b.p[i];
   if constexpr (sizeof(R) == 4) {
     float4 lo = b.plo[i];
@@ -172,17 +189,17 @@ __device__ __forceinline__ float kick_drift(const Geom &g, Dyn *__restrict__ d, 
       atomicOr(&d->err, (int)kErrRange);
     qout[i] = quantize(g, p, lo);
   } else {
-    p.x += dt * v.x;
-    p.y += dt * v.y;
-    p.z += dt * v.z;
+    p.x = fma(dt, v.x, p.x);
+    p.y = fma(dt, v.y, p.y);
+    p.z = fma(dt, v.z, p.z);
   }
   b.v[i] = v;
   b.p[i] = p;
   const float4 q = b.pb[i];
   const float zb = (float)p.w + q.z;
-  const float dx = (float)p.x - q.x - shear_tau * (zb - (float)kc<R>(g).half_Lz);
+  const float dx = fmaf(-shear_tau, zb - (float)kc<R>(g).half_Lz, (float)p.x - q.x);
   const float dy = (float)p.y - q.y, dz = (float)p.z - q.z;
-  return dx * dx + dy * dy + dz * dz;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
 // Largest value of v over the block, folded into d->maxdisp2 (one atomic per
@@ -582,17 +599,6 @@ __device__ __forceinline__ void lj_pair2_q(const SlotQ &G, const int4 &qa, const
 // (cz = dcz for a pair across the face, else 0), the time derivative of the
 // slot offset cz s(t).  Each thread evaluates its own side of a pair; the
 // shared theta_ij and the exact antisymmetry of d make F_ji = -F_ij.
-// Rounded operations that the compiler may not contract into FMAs: the DPD
-// pair arithmetic is written with them so that every kernel that inlines it
-// (a system's own step, a batch launch) computes the same bits.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <class R>
 __device__ __forceinline__ void dpd_pair(const Geom &g, const V4<R> &pi, const V4<R> &vi, int gi,
@@ -664,6 +670,9 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
   G.lz = R(g.lc[2]);
   G.s = R(d->s);
   const bool sample = mode != 1 && g.sample_every > 0 && (n1 % g.sample_every) == 0;
+  // mode 2 (the next step's kick and drift) exists only in FP32 without DPD
+  constexpr bool kCanFuse = sizeof(R) == 4 && !DPD;
+  const bool fused = kCanFuse && mode == 2;
   if (sample)
     for (int b = t; b < 3 * g.nbins; b += blockDim.x) s_prof[b] = 0;
   if (lane == 0) {
@@ -921,7 +930,9 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
     // Eq. 5: friction on the peculiar velocity plus the random force
     const V4<R> v = b.v[i];
     const R zu = pi.z + pi.w;  // unwrapped z (reference + displacement)
-    const R vs = K.shear * (zu - K.half_Lz);
+    // an explicitly rounded product: vs is subtracted below, and no kernel
+    // that inlines this may fuse it into an FMA
+    const R vs = mul_rn(K.shear, zu - K.half_Lz);
     R ftx = fx + tdx, fty = fy + tdy, ftz = fz + tdz;
     if (g.thermostat == 1 || g.thermostat == 2) {
       // 1: friction on the peculiar velocity (Eq. 5); 2: on the absolute
@@ -936,34 +947,35 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
       const R vf = g.thermostat == 1
                        ? vs
                        : (zu >= K.Lz ? K.shear_Lz : (zu < R(0) ? -K.shear_Lz : R(0)));
-      ftx += -xm * (v.x - vf) + amp * u[0];
-      fty += -xm * v.y + amp * u[1];
-      ftz += -xm * v.z + amp * u[2];
+      ftx += fma(amp, u[0], -xm * (v.x - vf));
+      fty += fma(amp, u[1], -xm * v.y);
+      ftz += fma(amp, u[2], -xm * v.z);
     }
     V4<R> nv = v;
     if (mode != 1) {
       const R half = K.half_dt_m;
-      nv.x = v.x + half * ftx;
-      nv.y = v.y + half * fty;
-      nv.z = v.z + half * ftz;
+      nv.x = fma(half, ftx, v.x);
+      nv.y = fma(half, fty, v.y);
+      nv.z = fma(half, ftz, v.z);
     }
     // fused with the next drift (mode 2), the total force goes straight into
     // the next half kick and neither force is stored
-    if (mode != 2) {
+    if (!fused) {
       b.fc[i] = make4<R>(fx, fy, fz, R(0));
       b.ft[i] = make4<R>(ftx, fty, ftz, R(0));
     }
     // DPD reads the other particles' half-step velocities: the kicked ones go
     // to a scratch array, copied back once every thread has read
     if constexpr (DPD) reinterpret_cast<V4<R> *>(w.vnew)[i] = nv;
-    else if (mode != 2) b.v[i] = nv;
+    else if (!fused) b.v[i] = nv;
     if (!isfinite(ftx + fty + ftz) || !isfinite(nv.x + nv.y + nv.z))
       atomicOr(&d->err, (int)kErrNonfinite);
     if (sample) {
       const R m = K.mass;
       const R vpx = nv.x - vs;
-      sxz = m * vpx * nv.z + R(0.5) * vir;
-      ke = m * (vpx * vpx + nv.y * nv.y + nv.z * nv.z);
+      // explicit fma (the same rounding in every instantiation)
+      sxz = fma(m * vpx, nv.z, R(0.5) * vir);
+      ke = m * fma(nv.z, nv.z, fma(nv.y, nv.y, vpx * vpx));
       R zw = zu, vw = nv.x;
       const R Lz = K.Lz;
       if (zw >= Lz) {
@@ -982,14 +994,14 @@ __device__ __forceinline__ void force_body(const Geom &g, Dyn *__restrict__ d, B
     // mode 2: the next step's first half kick and drift (FP32 without DPD,
     // where neighbours are read only through the fixed-point copy q; the
     // drifted copy goes to q2)
-    if constexpr (sizeof(R) == 4 && !DPD) {
-      if (mode == 2)
+    if constexpr (kCanFuse) {
+      if (fused)
         disp2 = kick_drift<R>(g, d, b, b.q2, i, nv, make4<R>(ftx, fty, ftz, R(0)),
                               drift_shear_tau(g, d));
     }
   }
-  if constexpr (sizeof(R) == 4 && !DPD) {
-    if (mode == 2) {
+  if constexpr (kCanFuse) {
+    if (fused) {
       block_max_disp<kForceWarps>(d, disp2);
       if (t == 0 && bx() == 0) d->qflip = 1;
     }
@@ -1746,9 +1758,9 @@ __global__ void kb_rb_finish(const MemberDev<R> *__restrict__ mem) {
 
 template <class R, bool BONDS, bool DPD>
 __global__ void __launch_bounds__(kForceThreads, sizeof(R) == 8 ? 1 : DPD ? 2 : LE_FORCE_MINB32)
-    kb_force(const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
+    kb_force(const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M, int mode) {
   LE_MEMBER(kBForce);
-  force_body<R, BONDS, DPD>(q.g, q.d, q.s0, q.s1, q.w, 0, VBlock{bx_});
+  force_body<R, BONDS, DPD>(q.g, q.d, q.s0, q.s1, q.w, mode, VBlock{bx_});
 }
 
 template <class R>
@@ -1760,12 +1772,12 @@ __global__ void __launch_bounds__(256) kb_vcopy(const MemberDev<R> *__restrict__
 #undef LE_MEMBER
 
 template <class R>
-void batch_step(const BatchGrid &bg, cudaStream_t st) {
+void batch_step(const BatchGrid &bg, cudaStream_t st, bool drift, int mode) {
   const MemberDev<R> *mem = static_cast<const MemberDev<R> *>(bg.mem);
   const int M = bg.M;
   const int *off = bg.off;
   const int n256 = bg.blocks[kB256];
-  kb_drift<R><<<n256, kDriftThreads, 0, st>>>(mem, off, M);
+  if (drift) kb_drift<R><<<n256, kDriftThreads, 0, st>>>(mem, off, M);
   kb_decide<R><<<M, 128, 0, st>>>(mem);
   kb_rb_bin<R><<<n256, 256, 0, st>>>(mem, off, M);
   launch_batch_sort(bg, st);
@@ -1777,13 +1789,13 @@ void batch_step(const BatchGrid &bg, cudaStream_t st) {
   const size_t smem = sizeof(long long) * 3 * (size_t)bg.nbins;
   const int nf = bg.blocks[kBForce];
   if (bg.dpd) {
-    if (bg.bonds) kb_force<R, true, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
-    else kb_force<R, false, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+    if (bg.bonds) kb_force<R, true, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M, 0);
+    else kb_force<R, false, true><<<nf, bg.force_threads, smem, st>>>(mem, off, M, 0);
     kb_vcopy<R><<<n256, 256, 0, st>>>(mem, off, M);
   } else if (bg.bonds) {
-    kb_force<R, true, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+    kb_force<R, true, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M, mode);
   } else {
-    kb_force<R, false, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M);
+    kb_force<R, false, false><<<nf, bg.force_threads, smem, st>>>(mem, off, M, mode);
   }
 }
 
@@ -1931,9 +1943,11 @@ void launch_observe(const SysDev &s, cudaStream_t st) {
 #undef FN
 }
 
-void launch_batch_step(const BatchGrid &bg, cudaStream_t st) {
-  if (bg.prec == 1) batch_step<float>(bg, st);
-  else batch_step<double>(bg, st);
+void launch_batch_step(const BatchGrid &bg, cudaStream_t st, bool drift, bool fuse) {
+  const bool can = batch_can_fuse_drift(bg);
+  const int mode = fuse && can ? 2 : 0;
+  if (bg.prec == 1) batch_step<float>(bg, st, drift || !can, mode);
+  else batch_step<double>(bg, st, true, 0);
 }
 
 }  // namespace le

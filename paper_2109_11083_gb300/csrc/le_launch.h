@@ -129,8 +129,12 @@ struct BatchGrid {
   int prec = 1, bonds = 0, dpd = 0;
   int force_threads = 256, list_threads = 128, nbins = 1, passes = 1;
 };
-// One step of every member of the group (drift, decide, gated rebuild, force).
-void launch_batch_step(const BatchGrid &bg, cudaStream_t st);
+// One step of every member of the group (drift, decide, gated rebuild,
+// force).  drift = false skips the drift launch (the previous step's force
+// launch ran it); fuse = true runs the next step's drift inside this step's
+// force launch (mode 2: only where batch_can_fuse_drift).
+void launch_batch_step(const BatchGrid &bg, cudaStream_t st, bool drift = true, bool fuse = false);
+inline bool batch_can_fuse_drift(const BatchGrid &bg) { return bg.prec == 1 && !bg.dpd; }
 void launch_batch_sort(const BatchGrid &bg, cudaStream_t st);  // gated radix sort, all passes
 
 __device__ __forceinline__ int batch_member(const int *off, int M, int bid) {
