@@ -288,6 +288,23 @@ def force_launch_bytes(n: int, mean_nb: float, fused_drift: bool = False) -> flo
     return force_kernel_bytes(n, mean_nb) + n * (16 + 4 + 16 + 16)
 
 
+def alu_check(le, n: int, mean_nb: float, launch_s: float):
+    """Secondary check of the pair kernel against the CUDA cores' FP32 peak
+    (measured by le_fp32_peak, outside the timed region): 21 flops per listed
+    pair (r^2 5, reciprocal 1, scaling 1, r^-6 2, LJ factor 4, force and
+    virial sums 8; an FMA is 2), every list entry evaluated."""
+    try:
+        fma, fma2 = le.le_fp32_peak()
+    except Exception as e:  # reported, not fatal: the line's roofline is HBM
+        return {"error": str(e)}
+    flops = 21.0 * n * mean_nb / launch_s * 1e-12
+    return {"bound": "alu", "flops_per_pair": 21, "achieved_tflops": flops,
+            "peak_tflops_fma": fma, "peak_tflops_fma2": fma2,
+            "frac_of_fma2_peak": flops / fma2 if fma2 > 0 else None,
+            "what": "k_force FP32 arithmetic (paired fma.rn.f32x2 form) against the measured "
+                    "CUDA-core FMA throughput; the kernel is bound by its L1 gathers"}
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -469,6 +486,7 @@ def run_ours(args):
                                    "rest": (total_ms - force_ms - drift_ms) / args.steps},
             "rebuilds": rebuilds, "image_rebuilds": c1["image_rebuilds"] - c0["image_rebuilds"],
             "mean_list_length": mean_nb,
+            "alu_check": alu_check(le, w.n, mean_nb, f_avg_s),
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
         line.update(sub)

@@ -328,6 +328,17 @@ LE_API le_status le_forces_noalloc(const double box[3], double shear_rate, doubl
 LE_API le_status le_sort_cell_keys(int64_t n, const uint32_t *keys, int bits, uint32_t *order,
                                    uint32_t *sorted_keys, void *cuda_stream);
 
+/* Measurement aid, not a step of the method: the FP32 arithmetic peak of the
+ * CUDA cores of the current device in TFLOP/s, an FMA counted as 2 flops,
+ * for scalar FMAs (tflops_fma) and for the paired fma.rn.f32x2 form
+ * (tflops_fma2) that the pair kernel uses.  Best of three timed rounds of
+ * independent FMA chains on 8 blocks per SM (about 40 GFLOP each, well under
+ * a second).  It allocates and frees a small device buffer and synchronises
+ * the default stream.  It backs the arithmetic cross-check of the pair
+ * kernel, whose roofline is HBM.  Errors: LE_ERR_INVALID_ARG (a NULL
+ * output), LE_ERR_CUDA. */
+LE_API le_status le_fp32_peak(double *tflops_fma, double *tflops_fma2);
+
 LE_API le_status le_destroy(le_sim *s);
 LE_API const char *le_last_error(const le_sim *s);
 LE_API const char *le_status_string(le_status st);

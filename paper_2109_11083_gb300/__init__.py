@@ -120,6 +120,7 @@ def lib():
                 "le_sort_cell_keys": (C.c_int, [C.c_int64, C.POINTER(C.c_uint32), C.c_int,
                                                 C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                 _P]),
+                "le_fp32_peak": (C.c_int, [_D, _D]),
                 "le_destroy": (C.c_int, [_P]),
                 "le_last_error": (C.c_char_p, [_P]),
                 "le_status_string": (C.c_char_p, [C.c_int]),
@@ -310,6 +311,13 @@ def le_sort_cell_keys(keys, bits: int, stream=None):
                                  _stream_handle(stream))
     _check(None, st)
     return order, out
+
+
+def le_fp32_peak():
+    """(scalar, paired) FP32 FMA throughput of the current device, TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(None, lib().le_fp32_peak(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def le_estimate_device_bytes(box, shear_rate: float, rc: float, skin: float, params: le_params,

@@ -62,3 +62,27 @@ def test_fused_calls_equal_single_steps_chains():
     for _ in range(64):
         b.step(1)
     _assert_same(a, b)
+
+
+def test_fused_call_rolls_back_on_error():
+    """A bond that breaks inside a multi-step FP32 call (fused pair and drift
+    launches, the fixed-point copies swapped every step) rolls the whole call
+    back: positions, velocities, forces and the step count are those before
+    the call, and the same call fails again the same way."""
+    pos = np.array([[2.0, 2.0, 2.0], [3.0, 2.0, 2.0], [5.0, 5.0, 5.0], [7.0, 7.0, 7.0]])
+    # the bond stretches 0.2 a step at first: past R0 = 1.5 a few steps in
+    vel = np.array([[-10.0, 0, 0], [10.0, 0, 0], [0, 0, 0], [0.5, 0, 0]])
+    sim = le.Sim(10.0, 0.1, 2 ** (1 / 6), 0.3, thermostat=0, dt=0.01, precision=le.LE_FP32)
+    sim.set_bonds([[0, 1]])
+    sim.set_particles(pos, vel)
+    r0, v0 = sim.positions()
+    f0 = sim.forces()
+    for _ in range(2):
+        with pytest.raises(le.LEError) as e:
+            sim.step(50)
+        assert e.value.status == 5
+        r1, v1 = sim.positions()
+        assert np.array_equal(r0, r1) and np.array_equal(v0, v1)
+        assert np.array_equal(f0, sim.forces())
+        assert sim.counters()["step"] == 0
+    sim.close()
