@@ -421,20 +421,26 @@ def run_ours(args):
             hv = _t.from_numpy(vel).pin_memory().numpy()
             out_p = _t.empty((w.n, 3), dtype=_t.float64).pin_memory().numpy()
             out_v = _t.empty((w.n, 3), dtype=_t.float64).pin_memory().numpy()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sim.set_particles(hp, hv)
-            sim.step(args.steps)
-            le.le_positions(sim.h, w.n, out_p, out_v)
-            sim.stress(instantaneous=False)
-            sim.velocity_profile()
-            torch.cuda.synchronize()
-            e_s = time.perf_counter() - t0
+            def e2e_once():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.set_particles(hp, hv)
+                sim.step(args.steps)
+                le.le_positions(sim.h, w.n, out_p, out_v)
+                sim.stress(instantaneous=False)
+                sim.velocity_profile()
+                torch.cuda.synchronize()
+                return time.perf_counter() - t0
+            # one untimed pass first: a call of K steps captures, once per
+            # process, the graph of its K mod 16 remaining steps
+            e2e_once()
+            e_s = e2e_once()
             e2e = {"value": w.n * args.steps / e_s, "unit": UNIT,
                    "h2d_bytes_per_step": 48 * w.n / args.steps,
                    "d2h_bytes_per_step": (48 * w.n + 8 * 3 + 16 * 20) / args.steps,
                    "what": "le_set_particles (host pinned pos/vel, initial list and forces) + "
-                           "le_step(K) + le_positions + le_stress + le_velocity_profile"}
+                           "le_step(K) + le_positions + le_stress + le_velocity_profile; "
+                           "the second of two passes (the first captures the step graphs)"}
         sub = {}
         if not args.no_sub and world == 1:
             # the metric's other half, bounded: batched and served forms against

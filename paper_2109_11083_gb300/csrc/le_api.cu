@@ -47,6 +47,10 @@ struct le_sim {
   long long *h_scalar = nullptr;     // pinned host scratch
   Dyn *h_dyn = nullptr;              // pinned mirror of the device record
   cudaGraphExec_t exec_chunk = nullptr, exec_one = nullptr;
+  // graphs of r = 2 .. kChunk-1 steps, captured when a call first ends with
+  // r steps after its whole chunks (the drift fused into the pair kernel
+  // across all r steps, as in a chunk)
+  cudaGraphExec_t exec_rem[kChunk] = {};
   bool eager = false;                // launch kernels directly (no graphs)
   bool dry_run = false;              // allocate() only counts bytes
   size_t device_bytes = 0;           // device memory of the particle buffers
@@ -94,11 +98,21 @@ template <class T> le_status dalloc(le_sim *s, T **p, size_t count) {
   return LE_OK;
 }
 
-void free_device(le_sim *s) {
-  for (long long &k : s->alloc_key) k = -1;
+// Every captured step graph of s (they hold the buffer addresses and the list
+// capacity of the capture).
+void destroy_graphs(le_sim *s) {
   if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
   if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
   s->exec_chunk = s->exec_one = nullptr;
+  for (cudaGraphExec_t &g : s->exec_rem) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+void free_device(le_sim *s) {
+  for (long long &k : s->alloc_key) k = -1;
+  destroy_graphs(s);
   for (void *p : s->allocs) cudaFree(p);
   s->allocs.clear();
   for (void *p : s->snap) cudaFree(p);
@@ -269,6 +283,8 @@ void choose_cells(le_sim *s) {
     g.lc[a] = g.L[a] / g.nc[a];
     g.ncell *= g.nc[a];
     g.inv_lc[a] = (float)(1.0 / g.lc[a]);
+    g.inv_lcd[a] = 1.0 / g.lc[a];
+    g.inv_L[a] = 1.0 / g.L[a];
     g.half_lc_f[a] = (float)(0.5 * g.lc[a] * (1.0 + 1e-6) + 1e-6);
     g.lc_hi[a] = (float)g.lc[a];
     g.lc_lo[a] = (float)(g.lc[a] - (double)g.lc_hi[a]);
@@ -622,16 +638,19 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
   if (n < 1 || n > kMaxParticles || !pos || !vel)
     return fail(s, LE_ERR_INVALID_ARG, "n out of range or null arrays");
   // non-finite coordinates or velocities are found by the import kernel
-  // bond table by particle id
-  std::vector<int> deg(n, 0);
-  for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
-    const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
-    if (i >= n || j >= n) return fail(s, LE_ERR_INVALID_ARG, "bond id out of range");
-    ++deg[i];
-    ++deg[j];
-  }
+  // bond table by particle id (host work only when there are bonds)
+  std::vector<int> deg;
   int maxb = 0;
-  for (int64_t i = 0; i < n; ++i) maxb = std::max(maxb, deg[i]);
+  if (!s->bonds.empty()) {
+    deg.assign(n, 0);
+    for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
+      const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
+      if (i >= n || j >= n) return fail(s, LE_ERR_INVALID_ARG, "bond id out of range");
+      ++deg[i];
+      ++deg[j];
+    }
+    for (int64_t i = 0; i < n; ++i) maxb = std::max(maxb, deg[i]);
+  }
   if (maxb > kMaxBonds) return fail(s, LE_ERR_INVALID_ARG, "more than 8 bonds on a particle");
   Geom &g = s->s.g;
   g.maxb = maxb;
@@ -642,15 +661,21 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
   maxnb = std::min<long long>(maxnb, n) < 8 ? 8 : maxnb;
   for (int attempt = 0; attempt < 4; ++attempt) {
     CKS(allocate(s, n, maxnb));
-    std::vector<int> bg((size_t)n * std::max(maxb, 1), -1);
-    std::fill(deg.begin(), deg.end(), 0);
-    for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
-      const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
-      bg[(size_t)i * maxb + deg[i]++] = j;
-      bg[(size_t)j * maxb + deg[j]++] = i;
+    if (maxb > 0) {
+      std::vector<int> bg((size_t)n * maxb, -1);
+      std::fill(deg.begin(), deg.end(), 0);
+      for (size_t b = 0; b < s->bonds.size() / 2; ++b) {
+        const int i = s->bonds[2 * b], j = s->bonds[2 * b + 1];
+        bg[(size_t)i * maxb + deg[i]++] = j;
+        bg[(size_t)j * maxb + deg[j]++] = i;
+      }
+      CK(cudaMemcpyAsync(s->s.w.bond_gid, bg.data(), sizeof(int) * bg.size(),
+                         cudaMemcpyHostToDevice, s->stream));
+      // the pageable copy has left bg by the time it returns
+    } else {
+      // no bonds: the one slot per particle holds -1 (every byte 0xFF)
+      CK(cudaMemsetAsync(s->s.w.bond_gid, 0xFF, sizeof(int) * (size_t)n, s->stream));
     }
-    CK(cudaMemcpyAsync(s->s.w.bond_gid, bg.data(), sizeof(int) * bg.size(), cudaMemcpyHostToDevice,
-                       s->stream));
     CKS(upload(s, s->s.stage, pos, 3 * (size_t)n, s->h_stage));
     CKS(upload(s, s->s.stage + 3 * n, vel, 3 * (size_t)n, s->h_stage + 3 * n));
     le_status st = initialise(s);
@@ -704,9 +729,11 @@ static le_status step_once(le_sim *s, int64_t nsteps) {
     CK(cudaGraphLaunch(s->exec_chunk, s->stream));
     left -= kChunk;
   }
-  while (left > 0) {
-    CK(cudaGraphLaunch(s->exec_one, s->stream));
-    --left;
+  if (left > 0) {
+    // the remaining steps as one graph (captured on first use)
+    cudaGraphExec_t &g = left == 1 ? s->exec_one : s->exec_rem[left];
+    if (!g) CKS(capture(s, (int)left, nullptr, &g));
+    CK(cudaGraphLaunch(g, s->stream));
   }
   launch_fold(s->s, s->stream);
   CK(cudaGetLastError());
@@ -727,9 +754,7 @@ static le_status grow_list(le_sim *s, int maxnb) {
   s->s.w.nbr = nullptr;
   CKS(dalloc(s, &s->s.w.nbr, (size_t)s->s.g.npad * (size_t)maxnb));
   s->s.g.maxnb = maxnb;
-  if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
-  if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
-  s->exec_chunk = s->exec_one = nullptr;
+  destroy_graphs(s);
   launch_relist(s->s, s->stream);
   CK(cudaGetLastError());
   return sync(s);
@@ -935,11 +960,7 @@ LE_API le_status le_get_counters(le_sim *s, le_counters *out) {
   return LE_OK;
 }
 
-static void drop_graphs(le_sim *s) {
-  if (s->exec_chunk) cudaGraphExecDestroy(s->exec_chunk);
-  if (s->exec_one) cudaGraphExecDestroy(s->exec_one);
-  s->exec_chunk = s->exec_one = nullptr;
-}
+static void drop_graphs(le_sim *s) { destroy_graphs(s); }
 
 LE_API le_status le_set_launch(le_sim *s, int force_threads, int list_threads) {
   if (!s) return LE_ERR_INVALID_ARG;

@@ -124,6 +124,7 @@ struct Geom {
   double eps, sigma, fene_k, fene_R0;
   double force_cap;               // > 0: LJ pair force magnitude limit (FP64 kernels)
   double lc[3];                   // cell edge
+  double inv_L[3], inv_lcd[3];    // 1 / box edge, 1 / cell edge (FP64; floor_div corrects)
   int nc[3];                      // cells per dimension
   int ncell;
   int n, npad;                    // particles, n rounded up to 32

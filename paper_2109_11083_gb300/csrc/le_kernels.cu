@@ -102,6 +102,17 @@ __device__ __forceinline__ void absolute_position(const Geom &g, const Bufs<R> &
   }
 }
 
+// floor(x / L) from a multiplication by 1/L, corrected so that the
+// remainder x - k L lies in [0, L): FP64 division is a long instruction
+// sequence on this GPU, a multiply and an FMA are not.
+__device__ __forceinline__ double floor_div(double x, double L, double invL) {
+  double k = floor(x * invL);
+  const double r = fma(-k, L, x);
+  if (r < 0.0) k -= 1.0;
+  else if (r >= L) k += 1.0;
+  return k;
+}
+
 // LE wrap of Eq. 4 at image offset dX: through the top face z -= Lz,
 // x -= dX, vx -= shear_rate*Lz; through the bottom face the mirror image;
 // x and y periodic.  Returns the z image index that was removed.
@@ -124,9 +135,9 @@ __device__ __forceinline__ int le_wrap(const Geom &g, double dX, double x[3], do
       x[2] = 0.0;  // within rounding of the bottom face: no image change
     }
   }
-  x[0] -= Lx * floor(x[0] / Lx);
+  x[0] -= Lx * floor_div(x[0], Lx, g.inv_L[0]);
   if (x[0] >= Lx) x[0] -= Lx;
-  x[1] -= Ly * floor(x[1] / Ly);
+  x[1] -= Ly * floor_div(x[1], Ly, g.inv_L[1]);
   if (x[1] >= Ly) x[1] -= Ly;
   return nz;
 }
@@ -135,7 +146,7 @@ __device__ __forceinline__ int cell_of(const Geom &g, const double x[3]) {
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    int k = (int)(x[a] / g.lc[a]);
+    const int k = (int)floor_div(x[a], g.lc[a], g.inv_lcd[a]);
     c[a] = k < 0 ? 0 : (k >= g.nc[a] ? g.nc[a] - 1 : k);
   }
   return c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
@@ -1195,7 +1206,7 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
     x[0] = x[1] = x[2] = vx = vy = vz = 0.0;
   }
   // any number of images away: remove whole boxes along z first
-  const double nzf = floor(x[2] / g.L[2]);
+  const double nzf = floor_div(x[2], g.L[2], g.inv_L[2]);
   if (nzf != 0.0) {
     x[2] -= nzf * g.L[2];
     x[0] -= nzf * d->dX;

@@ -200,6 +200,8 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
     if ((double)g.ncell * g.nc[a] > 1e8) return LE_ERR_INVALID_ARG;
     g.ncell *= g.nc[a];
     g.inv_lc[a] = (float)(1.0 / g.lc[a]);
+    g.inv_lcd[a] = 1.0 / g.lc[a];
+    g.inv_L[a] = 1.0 / g.L[a];
     g.half_lc_f[a] = (float)(0.5 * g.lc[a] * (1.0 + 1e-6) + 1e-6);
     g.lc_hi[a] = (float)g.lc[a];
     g.lc_lo[a] = (float)(g.lc[a] - (double)g.lc_hi[a]);
