@@ -69,3 +69,8 @@ def test_slot_encoding_gives_distinct_codes_below_the_end_marker():
                     assert 0 <= s < 255
                     seen.add(s)
     assert len(seen) == 144
+
+
+def test_fp32_peak_rejects_missing_outputs_without_a_gpu(lib):
+    """The FMA-peak measurement aid checks its arguments before any device work."""
+    assert lib.lib().le_fp32_peak(None, None) == 1
