@@ -257,7 +257,7 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
     CKS(dalloc(s, &w.key[k], n));
     CKS(dalloc(s, &w.val[k], n));
   }
-  s->s.sort_blocks = (int)((n + kSortTile - 1) / kSortTile);
+  s->s.sort_blocks = sort_blocks_for(n);
   CKS(dalloc(s, &w.hist, (size_t)kSortBuckets * s->s.sort_blocks));
   CKS(dalloc(s, &s->s.sort_part, sort_scan_parts(s->s.sort_blocks)));
   CKS(dalloc(s, &w.acc_prof, 3 * (size_t)g.nbins));

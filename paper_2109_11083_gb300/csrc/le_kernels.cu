@@ -1480,8 +1480,10 @@ __device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d,
       double nz = 0.0;
       if (dd[2] > 0.5 * g.L[2]) { dd[2] -= g.L[2]; dd[0] -= dXb; nz = 1.0; }
       else if (dd[2] < -0.5 * g.L[2]) { dd[2] += g.L[2]; dd[0] += dXb; nz = -1.0; }
-      dd[0] -= g.L[0] * rint(dd[0] / g.L[0]);
-      dd[1] -= g.L[1] * rint(dd[1] / g.L[1]);
+      // quotients by multiplication with the stored inverses: each is within
+      // rounding of an integer or of zero, far from a rint tie
+      dd[0] -= g.L[0] * rint(dd[0] * g.inv_L[0]);
+      dd[1] -= g.L[1] * rint(dd[1] * g.inv_L[1]);
       int cj[3];
       cell_coords(g, __float_as_int(b.pb[j].w), cj[0], cj[1], cj[2]);
       // off = X_ref(i) - X_ref(j) - image shift, shift = (x_i - x_j) - d
@@ -1490,10 +1492,10 @@ __device__ __forceinline__ void rb_bonds_body(const Geom g, Dyn *__restrict__ d,
         const double shift = (xi[a] - xj[a]) - dd[a];
         off[a] = (double)(ck[a] - cj[a]) * g.lc[a] - shift;
       }
-      const int dcz = (int)rint(off[2] / g.lc[2]);
-      const int dcy = (int)rint(off[1] / g.lc[1]);
+      const int dcz = (int)rint(off[2] * g.inv_lcd[2]);
+      const int dcy = (int)rint(off[1] * g.inv_lcd[1]);
       const int cross = nz != 0.0 ? 1 : 0;
-      const int kk = (int)rint((off[0] - (cross ? (double)dcz * fb : 0.0)) / g.lc[0]);
+      const int kk = (int)rint((off[0] - (cross ? (double)dcz * fb : 0.0)) * g.inv_lcd[0]);
       if (dcz < -1 || dcz > 1 || dcy < -1 || dcy > 1 || kk < -3 || kk > 4 ||
           (cross && dcz == 0)) {
         atomicOr(&d->err, (int)kErrSlot);

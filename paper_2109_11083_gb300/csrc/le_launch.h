@@ -17,7 +17,6 @@ constexpr int kForceThreads = 256;
 constexpr int kListMaxThreads = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;   // keys per thread and sort tile
-constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortMaxDigitBits = 9;
 constexpr int kSortBuckets = 1 << kSortMaxDigitBits;
 
@@ -83,6 +82,8 @@ void launch_observe(const SysDev &s, cudaStream_t st);    // partials[b][0:9] st
 void launch_tables(const SysDev &s, cudaStream_t st);  // slot tables from dyn->s and dyn->f_build
 
 int sort_passes_for(int bits);
+// tiles (blocks) of one radix pass over n keys
+int sort_blocks_for(int64_t n);
 size_t sort_scan_parts(int blocks);
 void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,
                       int bits, int blocks, cudaStream_t st);

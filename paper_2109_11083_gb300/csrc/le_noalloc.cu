@@ -257,7 +257,7 @@ size_t carve(SysDev &s, unsigned char *base, int64_t n) {
     w.key[k] = cv.take<uint32_t>(n);
     w.val[k] = cv.take<uint32_t>(n);
   }
-  s.sort_blocks = (int)((n + kSortTile - 1) / kSortTile);
+  s.sort_blocks = sort_blocks_for(n);
   s.sort_passes = sort_passes_for(g.sort_bits);
   w.hist = cv.take<uint32_t>((size_t)kSortBuckets * s.sort_blocks);
   s.sort_part = cv.take<uint32_t>(sort_scan_parts(s.sort_blocks));

@@ -9,6 +9,8 @@
 // it are deterministic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "le_launch.h"
 
 namespace le {
@@ -20,6 +22,13 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
+// Keys per thread of each of the nblocks tiles (1 to kSortItems): a small
+// sort runs more, shorter tiles in parallel (see sort_blocks_for).
+__device__ __forceinline__ int sort_tile_items(int n, int nblocks) {
+  const int per = nblocks * kSortThreads;
+  return (n + per - 1) / per;
+}
+
 __device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, int n, int shift,
                                              int bits, int nblocks, uint32_t *__restrict__ hist,
                                              int bx) {
@@ -28,9 +37,10 @@ __device__ __forceinline__ void rs_hist_body(const uint32_t *__restrict__ key, i
   const uint32_t mask = (uint32_t)nb - 1u;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
-  const int base = bx * kSortTile;
+  const int items = sort_tile_items(n, nblocks);
+  const int base = bx * kSortThreads * items;
 #pragma unroll 4
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < items; ++k) {
     const int i = base + k * kSortThreads + threadIdx.x;
     if (i < n) atomicAdd(&cnt[(key[i] >> shift) & mask], 1u);
   }
@@ -104,7 +114,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *__restrict_
   scan_top_body(part, np, (int)blockIdx.x);
 }
 
-// Pass 3: exclusive scan inside each chunk, offset by the chunk's start.
+// Pass 3: exclusive scan inside each chunk, offset by the chunk's start
+// (part == nullptr: a table of one chunk, scanned by this pass alone).
 __device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m,
                                                 const uint32_t *__restrict__ part, int bx) {
   __shared__ uint32_t wt[32];
@@ -115,7 +126,7 @@ __device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m,
     v[k] = base + k < m ? a[base + k] : 0u;
     s += v[k];
   }
-  uint32_t run = block_incl_scan(s, wt) - s + part[bx];
+  uint32_t run = block_incl_scan(s, wt) - s + (part ? part[bx] : 0u);
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     if (base + k < m) a[base + k] = run;
@@ -125,6 +136,39 @@ __device__ __forceinline__ void scan_apply_body(uint32_t *__restrict__ a, int m,
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(
     uint32_t *__restrict__ a, int m, const uint32_t *__restrict__ part) {
   scan_apply_body(a, m, part, (int)blockIdx.x);
+}
+
+// A table of up to kScanSeqChunks chunks scanned by one block, chunk after
+// chunk with the running total carried: one launch instead of three for a
+// small sort.
+constexpr int kScanSeqChunks = 8;
+__device__ __forceinline__ void scan_seq_body(uint32_t *__restrict__ a, int m) {
+  __shared__ uint32_t wt[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int c = 0; c * kScanChunk < m; ++c) {
+    const int base = c * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = base + k < m ? a[base + k] : 0u;
+      s += v[k];
+    }
+    const uint32_t incl = block_incl_scan(s, wt);
+    uint32_t run = incl - s + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < m) a[base + k] = run;
+      run += v[k];
+    }
+    __syncthreads();  // every thread has read carry and the warp totals
+    if (threadIdx.x == kScanThreads - 1) carry += incl;
+    __syncthreads();
+  }
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_seq(uint32_t *__restrict__ a, int m) {
+  scan_seq_body(a, m);
 }
 
 __device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin,
@@ -144,8 +188,9 @@ __device__ __forceinline__ void rs_scatter_body(const uint32_t *__restrict__ kin
     for (int w = 0; w < kWarps; ++w) wcnt[w][b] = 0;
   }
   __syncthreads();
-  const int tile = bx * kSortTile;
-  for (int c = 0; c < kSortItems; ++c) {
+  const int items = sort_tile_items(n, nblocks);
+  const int tile = bx * kSortThreads * items;
+  for (int c = 0; c < items; ++c) {
     const int i = tile + c * kSortThreads + t;
     const bool valid = i < n;
     const uint32_t k = valid ? kin[i] : 0u;
@@ -212,7 +257,9 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_sums(const MemberDev<R> 
   if (!q.d->rebuild) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
-  scan_sums_body(q.w.hist, (1 << w) * q.sort_blocks, q.sort_part, (int)blockIdx.x - off[m]);
+  const int mm = (1 << w) * q.sort_blocks;
+  if (mm <= kScanSeqChunks * kScanChunk) return;  // a small table: scan_apply's first block
+  scan_sums_body(q.w.hist, mm, q.sort_part, (int)blockIdx.x - off[m]);
 }
 
 template <class R>
@@ -223,6 +270,7 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
   const int mm = (1 << w) * q.sort_blocks;
+  if (mm <= kScanSeqChunks * kScanChunk) return;
   scan_top_body(q.sort_part, (mm + kScanChunk - 1) / kScanChunk, 0);
 }
 
@@ -234,7 +282,13 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const MemberDev<R>
   if (!q.d->rebuild) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
-  scan_apply_body(q.w.hist, (1 << w) * q.sort_blocks, q.sort_part, (int)blockIdx.x - off[m]);
+  const int mm = (1 << w) * q.sort_blocks;
+  const int bx = (int)blockIdx.x - off[m];
+  if (mm <= kScanSeqChunks * kScanChunk) {
+    if (bx == 0) scan_seq_body(q.w.hist, mm);  // the member's whole table
+    return;
+  }
+  scan_apply_body(q.w.hist, mm, q.sort_part, bx);
 }
 
 template <class R>
@@ -271,6 +325,16 @@ void batch_sort_passes(const BatchGrid &bg, cudaStream_t st) {
 
 int sort_passes_for(int bits) { return (bits + kSortMaxDigitBits - 1) / kSortMaxDigitBits; }
 
+// Tiles of kSortThreads x items keys: items = kSortItems for a large sort,
+// fewer (down to one) when that would leave fewer than ~2 tiles per SM of a
+// GB300, so that a small system's passes spread over the GPU instead of
+// running a few long tiles.  Any tiling gives the same stable order.
+int sort_blocks_for(int64_t n) {
+  const int64_t per = kSortThreads, spread = 304;
+  const int64_t items = std::min<int64_t>(kSortItems, std::max<int64_t>(1, (n + per * spread - 1) / (per * spread)));
+  return (int)((n + per * items - 1) / (per * items));
+}
+
 size_t sort_scan_parts(int blocks) {
   return ((size_t)kSortBuckets * blocks + kScanChunk - 1) / kScanChunk;
 }
@@ -294,9 +358,13 @@ void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32
     const int m = (1 << w) * blocks;
     const int np = (m + kScanChunk - 1) / kScanChunk;
     k_rs_hist<<<blocks, kSortThreads, 0, st>>>(key[in], n, shift, w, blocks, hist);
-    k_scan_sums<<<np, kScanThreads, 0, st>>>(hist, m, part);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(part, np);
-    k_scan_apply<<<np, kScanThreads, 0, st>>>(hist, m, part);
+    if (np > kScanSeqChunks) {
+      k_scan_sums<<<np, kScanThreads, 0, st>>>(hist, m, part);
+      k_scan_top<<<1, kScanThreads, 0, st>>>(part, np);
+      k_scan_apply<<<np, kScanThreads, 0, st>>>(hist, m, part);
+    } else {
+      k_scan_seq<<<1, kScanThreads, 0, st>>>(hist, m);  // a small table: one block
+    }
     k_rs_scatter<<<blocks, kSortThreads, 0, st>>>(key[in], val[in], key[out], val[out], n, shift,
                                                   w, blocks, hist);
   }
@@ -326,7 +394,7 @@ extern "C" LE_API le_status le_sort_cell_keys(int64_t n, const uint32_t *keys, i
     for (int64_t i = 0; i < n; ++i)
       if (keys[i] >> bits) return LE_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const int blocks = (int)((n + kSortTile - 1) / kSortTile);
+  const int blocks = sort_blocks_for(n);
   const size_t nb = sizeof(uint32_t) * (size_t)n;
   uint32_t *buf = nullptr;  // key[0], key[1], val[0], val[1], hist, part
   const size_t hist = (size_t)kSortBuckets * blocks, part = sort_scan_parts(blocks);
