@@ -216,6 +216,8 @@ le_status allocate(le_sim *s, int64_t n, int maxnb) {
   Geom &g = s->s.g;
   const int prec = s->s.prec;
   g.n = (int)n;
+  g.inv_volume = 1.0 / (g.L[0] * g.L[1] * g.L[2]);
+  g.inv_dof = 1.0 / (n > 1 ? 3.0 * (double)n - 3.0 : 1.0);
   g.npad = (int)((n + 31) / 32 * 32);
   g.maxnb = maxnb;
   const size_t vb = vec_bytes(prec);

@@ -125,6 +125,7 @@ struct Geom {
   double force_cap;               // > 0: LJ pair force magnitude limit (FP64 kernels)
   double lc[3];                   // cell edge
   double inv_L[3], inv_lcd[3];    // 1 / box edge, 1 / cell edge (FP64; floor_div corrects)
+  double inv_volume, inv_dof;     // 1 / V and 1 / (3n - 3) (1 for one particle): sample folds
   int nc[3];                      // cells per dimension
   int ncell;
   int n, npad;                    // particles, n rounded up to 32

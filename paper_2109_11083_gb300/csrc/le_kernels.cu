@@ -294,27 +294,34 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
   }
   __syncthreads();
   if (t == 0) {
+    // every field this thread reads, loaded together before the first store
+    const int qflip = d->qflip, qpar = d->qpar;
+    const long long acc_sxz = d->acc_sxz, acc_ke = d->acc_ke;
+    const long long n1 = d->step + 1;
+    const unsigned maxdisp2 = d->maxdisp2;
+    const double dX_build = d->dX_build, f_build = d->f_build;
+    const long long build_step = d->build_step;
+    const int force_rebuild = d->force_rebuild;
     // a pair kernel fused with the drift wrote the new positions to q2
-    if (d->qflip) {
-      d->qpar ^= 1;
+    if (qflip) {
+      d->qpar = qpar ^ 1;
       d->qflip = 0;
     }
     if (pending) {
-      const double V = g.L[0] * g.L[1] * g.L[2];
-      d->sum_sxz += -(double)d->acc_sxz * kInvFix / V;
-      d->sum_tpec += (double)d->acc_ke * kInvFix / (g.n > 1 ? 3.0 * g.n - 3.0 : 1.0);
+      // 1 / V and 1 / (3n - 3) come with the geometry (no FP64 division here)
+      d->sum_sxz += -(double)acc_sxz * kInvFix * g.inv_volume;
+      d->sum_tpec += (double)acc_ke * kInvFix * g.inv_dof;
       d->nsamples += 1;
       d->acc_sxz = 0;
       d->acc_ke = 0;
       d->pending = 0;
     }
-    const long long n1 = d->step + 1;
     const double dX1 = image_offset(g, n1);
-    const float maxd = sqrtf(__uint_as_float(d->maxdisp2));
+    const float maxd = sqrtf(__uint_as_float(maxdisp2));
     d->maxdisp2 = 0u;
     // continuous change of the image offset since the build (dX is reduced
     // modulo Lx; the shear sign tells which way it wrapped)
-    double ds = dX1 - d->dX_build;
+    double ds = dX1 - dX_build;
     if (g.shear_rate > 0.0 && ds < -0.5 * g.L[0]) ds += g.L[0];
     if (g.shear_rate < 0.0 && ds > 0.5 * g.L[0]) ds -= g.L[0];
     const double margin = 1e-6 * g.rl;
@@ -324,13 +331,13 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
     // w_i - w_j + shear*tau*dz_build e_x; pairs across the face included,
     // since the drift of the image offset cancels their streaming
     // difference.  A pair that can reach rc has |dz_build| < rc + 2 maxd.
-    const double tau = (double)(n1 - d->build_step) * g.dt;
+    const double tau = (double)(n1 - build_step) * g.dt;
     const double shear_term = fabs(g.shear_rate) * tau * (g.rc + 2.0 * (double)maxd);
-    const bool need = d->force_rebuild || disp_need ||
+    const bool need = force_rebuild || disp_need ||
                       (2.0 * (double)maxd * (1.0 + 1e-6) + shear_term + margin >= g.skin);
     double s;
     if (need) {
-      int m = (int)floor(dX1 / g.lc[0]);
+      int m = (int)floor(dX1 * g.inv_lcd[0]);  // corrected to [0, lx) below
       double f = dX1 - (double)m * g.lc[0];
       if (f >= g.lc[0]) { f -= g.lc[0]; m += 1; }
       if (f < 0.0) { f += g.lc[0]; m -= 1; }
@@ -343,10 +350,10 @@ __device__ __forceinline__ void decide_body(const Geom g, Dyn *__restrict__ d, W
       d->list_entries = 0;
       cross_window(g, f, d);
       d->nrebuild += 1;
-      if (!disp_need && !d->force_rebuild) d->nimage += 1;
+      if (!disp_need && !force_rebuild) d->nimage += 1;
       s = f;
     } else {
-      s = d->f_build + ds;
+      s = f_build + ds;
     }
     d->s = s;
     d->s_f = (float)s;
@@ -400,9 +407,9 @@ __global__ void k_fold(Geom g, Dyn *__restrict__ d, Work w) {
   }
   __syncthreads();
   if (t == 0 && pending) {
-    const double V = g.L[0] * g.L[1] * g.L[2];
-    d->sum_sxz += -(double)d->acc_sxz * kInvFix / V;
-    d->sum_tpec += (double)d->acc_ke * kInvFix / (g.n > 1 ? 3.0 * g.n - 3.0 : 1.0);
+    // the same arithmetic as the fold in k_decide
+    d->sum_sxz += -(double)d->acc_sxz * kInvFix * g.inv_volume;
+    d->sum_tpec += (double)d->acc_ke * kInvFix * g.inv_dof;
     d->nsamples += 1;
     d->acc_sxz = 0;
     d->acc_ke = 0;

@@ -211,6 +211,8 @@ le_status setup_geom(Geom &g, const double box[3], double shear_rate, double rc,
   g.sort_bits = bits;
   set_fixed_point(g);
   g.n = (int)n;
+  g.inv_volume = 1.0 / (g.L[0] * g.L[1] * g.L[2]);
+  g.inv_dof = 1.0 / (n > 1 ? 3.0 * (double)n - 3.0 : 1.0);
   g.npad = (int)((n + 31) / 32 * 32);
   g.maxb = 0;
   const double V = g.L[0] * g.L[1] * g.L[2];
