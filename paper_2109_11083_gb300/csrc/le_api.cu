@@ -1169,6 +1169,15 @@ void batch_drop_graphs(le_batch *b) {
   b->groups.clear();
 }
 
+// Sort tiles of a batch member: always the full 16 keys per thread.  A batch
+// fills the GPU with many members, so the smaller tiles a system sorted on
+// its own gets (sort_blocks_for) would only add tiles and count-table
+// entries.  Fewer tiles than the member's own never outgrow its tables.
+int batch_sort_blocks(int64_t n) {
+  const int64_t tile = (int64_t)kSortThreads * kSortItems;
+  return (int)((n + tile - 1) / tile);
+}
+
 template <class R>
 void fill_members(const std::vector<le_sim *> &sims, std::vector<MemberDev<R>> &out) {
   out.resize(sims.size());
@@ -1187,7 +1196,7 @@ void fill_members(const std::vector<le_sim *> &sims, std::vector<MemberDev<R>> &
     m.w = sd.w;
     m.sort_part = sd.sort_part;
     m.sort_passes = sd.sort_passes;
-    m.sort_blocks = sd.sort_blocks;
+    m.sort_blocks = batch_sort_blocks(sd.g.n);
   }
 }
 
@@ -1221,10 +1230,10 @@ le_status batch_build_groups(le_batch *b) {
       cnt[kB256] = blocks_for(sd.g.n, 256);
       cnt[kBForce] = blocks_for(sd.g.n, bg.force_threads);
       cnt[kBList] = blocks_for(sd.g.n, bg.list_threads);
-      cnt[kBSort] = sd.sort_blocks;
+      cnt[kBSort] = batch_sort_blocks(sd.g.n);
       cnt[kBOne] = 1;
       for (int p = 0; p < kMaxSortPasses; ++p)
-        cnt[kBScan0 + p] = sort_scan_blocks(sd.g.sort_bits, sd.sort_blocks, p);
+        cnt[kBScan0 + p] = sort_scan_blocks(sd.g.sort_bits, batch_sort_blocks(sd.g.n), p);
       for (int kind = 0; kind < kBKinds; ++kind)
         off[(size_t)kind * M1 + k + 1] = off[(size_t)kind * M1 + k] + cnt[kind];
     }
