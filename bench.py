@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true",
                     help="batched workload: time the batch alone (no per-box comparison, "
                          "no tuning), for profiler captures")
+    ap.add_argument("--requests", type=int, default=200,
+                    help="served workload: requests taken from the seeded trace (of 1000)")
     ap.add_argument("--arrival-rate", type=float, default=50.0,
                     help="served workload: request arrivals per second (the trace's 50/s "
                          "arrival times stretched or compressed)")

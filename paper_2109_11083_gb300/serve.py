@@ -310,7 +310,7 @@ def main_bench(args) -> int:
     """`bench.py --workload served`: a Poisson stream of mixed LJ/KG shear-sweep
     requests served with continuous batching; p50/p99 latency and aggregate
     particle-steps/s."""
-    count = 200
+    count = max(1, int(getattr(args, "requests", 200)))
     steps = max(args.steps // 4, 50)
     rate = float(getattr(args, "arrival_rate", 50.0))
     rec = served_record(count, steps, rate)
