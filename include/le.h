@@ -339,6 +339,19 @@ LE_API le_status le_sort_cell_keys(int64_t n, const uint32_t *keys, int bits, ui
  * output), LE_ERR_CUDA. */
 LE_API le_status le_fp32_peak(double *tflops_fma, double *tflops_fma2);
 
+/* Failure-detection self-test, not a step of the method (the paper has no
+ * counterpart).  One warp waits, through the same bounded mbarrier wait that
+ * the pair kernel uses for its bulk copies of list rows, on a barrier that
+ * nothing completes.  The wait gives up after about one second (or 2^22
+ * polls, whichever comes first) and the call returns LE_ERR_TIMEOUT, the
+ * expected outcome, with the time the probe took in waited_ms (nullable):
+ * a copy that never lands in the pair kernel ends as a status the host reads,
+ * not as a hang, and the device stays usable.  Work runs on cuda_stream (NULL:
+ * the default stream); a small device buffer is allocated and freed inside.
+ * LE_OK would mean the wait completed, which cannot happen; LE_ERR_CUDA on a
+ * CUDA failure. */
+LE_API le_status le_wait_selftest(void *cuda_stream, double *waited_ms);
+
 LE_API le_status le_destroy(le_sim *s);
 LE_API const char *le_last_error(const le_sim *s);
 LE_API const char *le_status_string(le_status st);

@@ -121,6 +121,7 @@ def lib():
                                                 C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                                 _P]),
                 "le_fp32_peak": (C.c_int, [_D, _D]),
+                "le_wait_selftest": (C.c_int, [_P, _D]),
                 "le_destroy": (C.c_int, [_P]),
                 "le_last_error": (C.c_char_p, [_P]),
                 "le_status_string": (C.c_char_p, [C.c_int]),
@@ -318,6 +319,14 @@ def le_fp32_peak():
     a, b = C.c_double(), C.c_double()
     _check(None, lib().le_fp32_peak(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def le_wait_selftest(stream=None):
+    """(status, ms) of the bounded-wait self-test; status LE_ERR_TIMEOUT (8)
+    is the expected outcome."""
+    ms = C.c_double()
+    st = lib().le_wait_selftest(_stream_handle(stream), C.byref(ms))
+    return st, ms.value
 
 
 def le_estimate_device_bytes(box, shear_rate: float, rc: float, skin: float, params: le_params,

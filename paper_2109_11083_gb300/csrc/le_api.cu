@@ -535,6 +535,33 @@ LE_API void le_default_params(le_params *p) {
   p->profile_bins = 20;
 }
 
+LE_API le_status le_wait_selftest(void *cuda_stream, double *waited_ms) {
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int *flag = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaMalloc(&flag, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+  if (ce == cudaSuccess) {
+    launch_wait_probe(flag, st);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  int gave_up = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(&gave_up, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (flag) cudaFree(flag);
+  if (ce != cudaSuccess) return LE_ERR_CUDA;
+  if (waited_ms) *waited_ms = (double)ms;
+  return gave_up ? LE_ERR_TIMEOUT : LE_OK;
+}
+
 LE_API const char *le_status_string(le_status st) {
   switch (st) {
     case LE_OK: return "ok";

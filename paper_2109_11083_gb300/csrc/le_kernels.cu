@@ -419,8 +419,9 @@ __global__ void k_fold(Geom g, Dyn *__restrict__ d, Work w) {
 
 // ------------------------------------------------------------------ k_force
 // Bulk-copy (TMA, cp.async.bulk) helpers for streaming a warp's neighbour-list
-// rows into shared memory.  Waits are bounded: after kWaitLimit polls the
-// kernel records kErrTimeout instead of spinning on.
+// rows into shared memory.  Waits are bounded: after kWaitNs nanoseconds of
+// the global timer (or kWaitLimit polls, whichever comes first) the kernel
+// records kErrTimeout instead of spinning on.
 constexpr int kRowsPerChunk = 16;                  // 16 rows x 128 B = 2 KB per stage
 constexpr int kForceWarps = kForceThreads / 32;
 // neighbour gathers in flight per thread in the pair loop, and the FP32
@@ -442,6 +443,7 @@ constexpr int kForceUnroll = LE_FORCE_UNROLL;
 #endif
 constexpr int kListUnroll = LE_LIST_UNROLL;
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // one second
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -464,13 +466,24 @@ __device__ __forceinline__ void bulk_rows(void *dst, const void *src, uint32_t b
           smem_addr(dst)),
       "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once the phase of the given parity has completed; false after about
+// kWaitNs (the timer is read only once the first poll has failed)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  unsigned long long t0 = 0;
   for (uint32_t it = 0; it < kWaitLimit; ++it) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     if (ok) return true;
+    const unsigned long long now = global_ns();
+    if (it == 0) t0 = now;
+    else if (now - t0 > kWaitNs) return false;
   }
   return false;
 }
@@ -1819,7 +1832,21 @@ void batch_step(const BatchGrid &bg, cudaStream_t st, bool drift, int mode) {
   }
 }
 
+// Failure-detection self-test: one warp waits on an mbarrier that nothing
+// arrives on, through the same bounded wait as the pair kernel, and records
+// whether the wait gave up (1) or, impossibly, completed (0).
+__global__ void k_wait_probe(int *out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  mbar_init_fence();
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u);
+  if (threadIdx.x == 0) out[0] = ok ? 0 : 1;
+}
+
 }  // namespace
+
+void launch_wait_probe(int *out, cudaStream_t st) { k_wait_probe<<<1, 32, 0, st>>>(out); }
 
 // ------------------------------------------------------------------ launchers
 #define LE_DISPATCH(s, FN)            \

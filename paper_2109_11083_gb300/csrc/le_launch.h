@@ -71,6 +71,9 @@ void launch_relist(const SysDev &s, cudaStream_t st);
 // mode 2: mode 0 followed by the next step's kick and drift of each particle
 //         (FP32 without DPD only: can_fuse_drift), forces not stored.
 void launch_force(const SysDev &s, int mode, cudaStream_t st);
+// failure-detection self-test: out[0] = 1 once a wait on a barrier that
+// nothing completes has given up (the pair kernel's bounded wait)
+void launch_wait_probe(int *out, cudaStream_t st);
 // whether launch_force may run mode 2 for this system
 bool can_fuse_drift(const SysDev &s);
 void launch_fold(const SysDev &s, cudaStream_t st);
