@@ -29,6 +29,7 @@ namespace {
 constexpr int kChunk = 16;
 constexpr uint64_t kStateMagic = 0x4c45534d53544154ull;  // "LESMSTAT"
 constexpr int kStateVersion = 5;
+constexpr int kUpChunks = 4;
 }  // namespace
 
 struct le_sim {
@@ -38,6 +39,11 @@ struct le_sim {
   cudaStream_t stream = nullptr;     // where the work runs
   bool own_stream = false;
   cudaStream_t cap_main = nullptr, cap_side = nullptr;  // private capture streams
+  // le_set_particles: host -> device copies in kUpChunks pieces on up_stream,
+  // each piece imported on the main stream as soon as it has landed
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_ev[kUpChunks] = {};
+  cudaEvent_t up_go = nullptr;
   SysDev s;
   bool has_particles = false;
   int64_t n = 0;
@@ -137,12 +143,36 @@ bool is_pinned(const void *p) {
 }
 
 // Host -> device copy of n doubles from the caller's array into dst.
-le_status upload(le_sim *s, double *dst, const double *src, size_t n, double *stage_part) {
+le_status upload(le_sim *s, double *dst, const double *src, size_t n, double *stage_part,
+                 cudaStream_t st) {
   if (is_pinned(src)) {
-    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   } else {
     std::memcpy(stage_part, src, sizeof(double) * n);
-    CK(cudaMemcpyAsync(dst, stage_part, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dst, stage_part, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  }
+  return LE_OK;
+}
+
+// First particle of upload piece c of n (pieces of whole particles).
+int64_t up_piece(int64_t n, int c) { return n * c / kUpChunks; }
+
+// The caller's positions and velocities into the staging buffer, in
+// kUpChunks pieces on up_stream (after the main stream's earlier work), each
+// piece's end recorded in up_ev[c] for the import (initialise) to wait on.
+le_status upload_particles(le_sim *s, const double *pos, const double *vel) {
+  const int64_t n = s->n;
+  CK(cudaEventRecord(s->up_go, s->stream));
+  CK(cudaStreamWaitEvent(s->up_stream, s->up_go, 0));
+  for (int c = 0; c < kUpChunks; ++c) {
+    const int64_t a = up_piece(n, c), b = up_piece(n, c + 1);
+    if (b > a) {
+      CKS(upload(s, s->s.stage + 3 * a, pos + 3 * a, 3 * (size_t)(b - a), s->h_stage + 3 * a,
+                 s->up_stream));
+      CKS(upload(s, s->s.stage + 3 * n + 3 * a, vel + 3 * a, 3 * (size_t)(b - a),
+                 s->h_stage + 3 * n + 3 * a, s->up_stream));
+    }
+    CK(cudaEventRecord(s->up_ev[c], s->up_stream));
   }
   return LE_OK;
 }
@@ -499,7 +529,12 @@ le_status initialise(le_sim *s) {
   CK(cudaMemsetAsync(s->s.w.sum_prof, 0, 16 * (size_t)s->s.g.nbins, s->stream));
   CK(cudaMemsetAsync(s->s.w.cnt_prof, 0, 8 * (size_t)s->s.g.nbins, s->stream));
   launch_tables(s->s, s->stream);
-  launch_import(s->s, s->stream);
+  // each piece is imported once its copy has landed (the copies of the later
+  // pieces overlap the import of the earlier ones)
+  for (int c = 0; c < kUpChunks; ++c) {
+    CK(cudaStreamWaitEvent(s->stream, s->up_ev[c], 0));
+    launch_import(s->s, s->stream, (int)up_piece(s->n, c), (int)up_piece(s->n, c + 1));
+  }
   launch_rebuild(s->s, true, s->stream);
   CK(cudaGetLastError());
   CKS(read_dyn(s));
@@ -617,6 +652,10 @@ LE_API le_status le_create(const double box[3], double shear_rate, double rc, do
   }
   e = cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up_stream, cudaStreamNonBlocking);
+  for (int c = 0; c < kUpChunks && e == cudaSuccess; ++c)
+    e = cudaEventCreateWithFlags(&s->up_ev[c], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->up_go, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_scalar, 64);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_dyn, sizeof(Dyn));
   if (e != cudaSuccess) {
@@ -641,6 +680,13 @@ LE_API le_status le_destroy(le_sim *s) {
   if (s->h_dyn) cudaFreeHost(s->h_dyn);
   if (s->cap_main) cudaStreamDestroy(s->cap_main);
   if (s->cap_side) cudaStreamDestroy(s->cap_side);
+  if (s->up_stream) {
+    cudaStreamSynchronize(s->up_stream);
+    cudaStreamDestroy(s->up_stream);
+  }
+  for (cudaEvent_t ev : s->up_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (s->up_go) cudaEventDestroy(s->up_go);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
   return LE_OK;
@@ -705,8 +751,7 @@ LE_API le_status le_set_particles(le_sim *s, int64_t n, const double *pos, const
       // no bonds: the one slot per particle holds -1 (every byte 0xFF)
       CK(cudaMemsetAsync(s->s.w.bond_gid, 0xFF, sizeof(int) * (size_t)n, s->stream));
     }
-    CKS(upload(s, s->s.stage, pos, 3 * (size_t)n, s->h_stage));
-    CKS(upload(s, s->s.stage + 3 * n, vel, 3 * (size_t)n, s->h_stage + 3 * n));
+    CKS(upload_particles(s, pos, vel));
     le_status st = initialise(s);
     if (st == LE_ERR_CAPACITY && s->err.rfind("grow:", 0) == 0) {
       maxnb = std::stoi(s->err.substr(5));

@@ -1211,10 +1211,11 @@ __global__ void __launch_bounds__(256) k_rb_bin(const __grid_constant__ Geom g, 
 // images at the current offset, binned, displacement from the cell reference.
 template <class R>
 __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
-                                                Bufs<R> s1, Work w, const double *__restrict__ stage) {
+                                                Bufs<R> s1, Work w, const double *__restrict__ stage,
+                                                int i0, int i1) {
   const Bufs<R> b = pick(d->cur, s0, s1);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
+  const int i = i0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= i1) return;
   double x[3] = {stage[3 * (size_t)i], stage[3 * (size_t)i + 1], stage[3 * (size_t)i + 2]};
   double vx = stage[3 * (size_t)g.n + 3 * (size_t)i];
   double vy = stage[3 * (size_t)g.n + 3 * (size_t)i + 1];
@@ -1953,9 +1954,11 @@ void launch_relist(const SysDev &s, cudaStream_t st) {
   }
 }
 
-void launch_import(const SysDev &s, cudaStream_t st) {
-  const int nb = blocks_for(s.g.n, 256);
-#define FN(R, A, B) k_import<R><<<nb, 256, 0, st>>>(s.g, s.dyn, A, B, s.w, s.stage)
+void launch_import(const SysDev &s, cudaStream_t st, int i0, int i1) {
+  if (i1 < 0) i1 = s.g.n;
+  if (i1 <= i0) return;
+  const int nb = blocks_for(i1 - i0, 256);
+#define FN(R, A, B) k_import<R><<<nb, 256, 0, st>>>(s.g, s.dyn, A, B, s.w, s.stage, i0, i1)
   LE_DISPATCH(s, FN);
 #undef FN
 }

@@ -77,7 +77,8 @@ void launch_wait_probe(int *out, cudaStream_t st);
 // whether launch_force may run mode 2 for this system
 bool can_fuse_drift(const SysDev &s);
 void launch_fold(const SysDev &s, cudaStream_t st);
-void launch_import(const SysDev &s, cudaStream_t st);     // reads stage[0:3n] pos, [3n:6n] vel
+// reads stage[0:3n] pos, [3n:6n] vel; particles [i0, i1) (i1 < 0: to n)
+void launch_import(const SysDev &s, cudaStream_t st, int i0 = 0, int i1 = -1);
 void launch_export(const SysDev &s, cudaStream_t st);     // writes stage: pos, vel; and fc into partial-free area
 void launch_export_forces(const SysDev &s, cudaStream_t st);  // writes stage[0:3n] = Fc
 int observe_blocks(const SysDev &s);
