@@ -921,10 +921,31 @@ LE_API le_status le_forces(le_sim *s, double *out) {
 LE_API le_status le_positions(le_sim *s, double *pos, double *vel) {
   if (!s) return LE_ERR_INVALID_ARG;
   if (!s->has_particles) return fail(s, LE_ERR_STATE, "no particles");
+  const int64_t n = s->n;
+  if ((!pos || is_pinned(pos)) && (!vel || is_pinned(vel))) {
+    // pinned destinations: the output in kUpChunks pieces of caller ids, each
+    // copied back on up_stream while the next piece is exported
+    for (int c = 0; c < kUpChunks; ++c) {
+      const int64_t a = up_piece(n, c), b = up_piece(n, c + 1);
+      launch_export_ids(s->s, s->stream, (int)a, (int)b);
+      CK(cudaGetLastError());
+      CK(cudaEventRecord(s->up_ev[c], s->stream));
+      CK(cudaStreamWaitEvent(s->up_stream, s->up_ev[c], 0));
+      if (b > a && pos)
+        CK(cudaMemcpyAsync(pos + 3 * a, s->s.stage + 3 * a, sizeof(double) * 3 * (size_t)(b - a),
+                           cudaMemcpyDeviceToHost, s->up_stream));
+      if (b > a && vel)
+        CK(cudaMemcpyAsync(vel + 3 * a, s->s.stage + 3 * n + 3 * a,
+                           sizeof(double) * 3 * (size_t)(b - a), cudaMemcpyDeviceToHost,
+                           s->up_stream));
+    }
+    CK(cudaStreamSynchronize(s->up_stream));
+    return sync(s);
+  }
   launch_export(s->s, s->stream);
   CK(cudaGetLastError());
-  if (pos) CKS(download(s, pos, s->s.stage, 3 * (size_t)s->n, s->h_stage));
-  if (vel) CKS(download(s, vel, s->s.stage + 3 * s->n, 3 * (size_t)s->n, s->h_stage + 3 * s->n));
+  if (pos) CKS(download(s, pos, s->s.stage, 3 * (size_t)n, s->h_stage));
+  if (vel) CKS(download(s, vel, s->s.stage + 3 * n, 3 * (size_t)n, s->h_stage + 3 * n));
   return sync(s);
 }
 

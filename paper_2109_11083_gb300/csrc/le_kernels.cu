@@ -1288,8 +1288,8 @@ __device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ 
   dst.v[k] = src.v[o];
   const int gid = src.gid[o];
   dst.gid[k] = gid;
+  w.rank[gid] = k;  // the sorted slot of each particle id (exports, bonds)
   if (g.maxb > 0) {
-    w.rank[gid] = k;
     int cx, cy, czz;
     cell_coords(g, c, cx, cy, czz);
     double x0 = ((double)cx + 0.5) * g.lc[0] + (double)h.x;
@@ -1552,6 +1552,32 @@ __global__ void __launch_bounds__(256) k_export(Geom g, Dyn *__restrict__ d, Buf
   double vx = (double)v.x;
   le_wrap(g, d->dX, x, vx);
   const size_t o = 3 * (size_t)b.gid[i];
+  stage[o] = x[0];
+  stage[o + 1] = x[1];
+  stage[o + 2] = x[2];
+  const size_t q = 3 * (size_t)g.n + o;
+  stage[q] = vx;
+  stage[q + 1] = (double)v.y;
+  stage[q + 2] = (double)v.z;
+}
+
+// The same output for caller ids [g0, g1), read through the rank table:
+// consecutive threads write consecutive ids, so a piece of the output is
+// complete (and can be copied to the host) as soon as its launch is.
+template <class R>
+__global__ void __launch_bounds__(256) k_export_ids(Geom g, Dyn *__restrict__ d, Bufs<R> s0,
+                                                    Bufs<R> s1, const int *__restrict__ rank,
+                                                    double *__restrict__ stage, int g0, int g1) {
+  const Bufs<R> b = pick(d->cur, s0, s1);
+  const int id = g0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (id >= g1) return;
+  const int i = min(max(rank[id], 0), g.n - 1);
+  double x[3];
+  absolute_position<R>(g, b, i, x);
+  const V4<R> v = b.v[i];
+  double vx = (double)v.x;
+  le_wrap(g, d->dX, x, vx);
+  const size_t o = 3 * (size_t)id;
   stage[o] = x[0];
   stage[o + 1] = x[1];
   stage[o + 2] = x[2];
@@ -1966,6 +1992,14 @@ void launch_import(const SysDev &s, cudaStream_t st, int i0, int i1) {
 void launch_export(const SysDev &s, cudaStream_t st) {
   const int nb = blocks_for(s.g.n, 256);
 #define FN(R, A, B) k_export<R><<<nb, 256, 0, st>>>(s.g, s.dyn, A, B, s.stage)
+  LE_DISPATCH(s, FN);
+#undef FN
+}
+
+void launch_export_ids(const SysDev &s, cudaStream_t st, int g0, int g1) {
+  if (g1 <= g0) return;
+  const int nb = blocks_for(g1 - g0, 256);
+#define FN(R, A, B) k_export_ids<R><<<nb, 256, 0, st>>>(s.g, s.dyn, A, B, s.w.rank, s.stage, g0, g1)
   LE_DISPATCH(s, FN);
 #undef FN
 }

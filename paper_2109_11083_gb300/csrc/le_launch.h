@@ -80,6 +80,8 @@ void launch_fold(const SysDev &s, cudaStream_t st);
 // reads stage[0:3n] pos, [3n:6n] vel; particles [i0, i1) (i1 < 0: to n)
 void launch_import(const SysDev &s, cudaStream_t st, int i0 = 0, int i1 = -1);
 void launch_export(const SysDev &s, cudaStream_t st);     // writes stage: pos, vel; and fc into partial-free area
+// positions and velocities of caller ids [g0, g1) into the staging buffer
+void launch_export_ids(const SysDev &s, cudaStream_t st, int g0, int g1);
 void launch_export_forces(const SysDev &s, cudaStream_t st);  // writes stage[0:3n] = Fc
 int observe_blocks(const SysDev &s);
 void launch_observe(const SysDev &s, cudaStream_t st);    // partials[b][0:9] stress sums, [9] epot
