@@ -48,7 +48,7 @@ def _check(sim, p, step, prec, box, bonds):
         B = oracle.force_error_bound(p, dX, r, bonds, 2.0 ** -24, P)
         err = np.linalg.norm(f - F, axis=1)
         assert np.all(err <= B + 1e-5), (step, int(np.argmax(err - B)))
-        # the benchmark spec's tolerance itself (the WCA pair force vanishes at
+        # the 1e-5 relative force tolerance itself (the WCA pair force vanishes at
         # its cut-off 2^(1/6), so a cut-off decision moves no force)
         g, q = force_errors(f, F)
         assert g <= 1e-5 and q <= 1e-5, (step, g, q)

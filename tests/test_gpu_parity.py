@@ -91,7 +91,7 @@ def ref_extent(box, rc, skin, bonds=None):
 
 def assert_forces(f, ref, prec, what="", bound=None, band=None, rows=None,
                   particle_tol=FORCE_TOL):
-    """FP64: the benchmark spec's tolerance directly.  FP32: the same tolerance once
+    """FP64: the 1e-5 relative force tolerance directly.  FP32: the same tolerance once
     the band pairs' cut-off decisions are taken out (band = oracle.band_pairs
     output), and every particle within the rounding bound; particle_tol
     replaces the per-particle tolerance where the configuration's forces are

@@ -53,7 +53,7 @@ def test_noalloc_forces_equal_handle_forces_twice(prec):
             g, q = force_errors(f, F)
             assert g <= 1e-5 and q <= 1e-5, (call, g, q)
         else:
-            # against the oracle: the benchmark spec's tolerance once the band
+            # against the oracle: the 1e-5 relative force tolerance once the band
             # pairs' cut-off decisions are taken out
             P = 0.5 * box / math.floor(box / (rc + skin))
             band = 4.0 * math.sqrt(3.0) * 2.0 ** -24 * (6.0 * P + 2.0 * rc)
