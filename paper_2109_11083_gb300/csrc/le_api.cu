@@ -1230,6 +1230,7 @@ struct BatchGroup {
   le::BatchGrid grid;
   void *d_mem = nullptr;
   int *d_off = nullptr;
+  int *d_act = nullptr;  // rebuild tables, rewritten on the device every step
 };
 
 struct le_batch {
@@ -1258,6 +1259,7 @@ void batch_drop_graphs(le_batch *b) {
   for (BatchGroup &gr : b->groups) {
     if (gr.d_mem) cudaFree(gr.d_mem);
     if (gr.d_off) cudaFree(gr.d_off);
+    if (gr.d_act) cudaFree(gr.d_act);
   }
   b->groups.clear();
 }
@@ -1325,8 +1327,10 @@ le_status batch_build_groups(le_batch *b) {
       cnt[kBList] = blocks_for(sd.g.n, bg.list_threads);
       cnt[kBSort] = batch_sort_blocks(sd.g.n);
       cnt[kBOne] = 1;
-      for (int p = 0; p < kMaxSortPasses; ++p)
+      for (int p = 0; p < kMaxSortPasses; ++p) {
         cnt[kBScan0 + p] = sort_scan_blocks(sd.g.sort_bits, batch_sort_blocks(sd.g.n), p);
+        if (sort_scan_large(sd.g.sort_bits, batch_sort_blocks(sd.g.n), p)) bg.scan_large[p] = true;
+      }
       for (int kind = 0; kind < kBKinds; ++kind)
         off[(size_t)kind * M1 + k + 1] = off[(size_t)kind * M1 + k] + cnt[kind];
     }
@@ -1344,13 +1348,17 @@ le_status batch_build_groups(le_batch *b) {
       host_mem = md.data();
       mem_bytes = md.size() * sizeof(MemberDev<double>);
     }
+    const size_t act_bytes = (size_t)kBKinds * batch_act_stride(bg.M) * sizeof(int);
     cudaError_t ce = cudaMalloc(&gr.d_mem, mem_bytes);
     if (ce == cudaSuccess) ce = cudaMalloc(&gr.d_off, off.size() * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc(&gr.d_act, act_bytes);
+    if (ce == cudaSuccess) ce = cudaMemset(gr.d_act, 0, act_bytes);  // no member listed
     if (ce == cudaSuccess) ce = cudaMemcpy(gr.d_mem, host_mem, mem_bytes, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
       ce = cudaMemcpy(gr.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
     bg.mem = gr.d_mem;
     bg.off = gr.d_off;
+    bg.act = gr.d_act;
     b->groups.push_back(gr);
     if (ce != cudaSuccess) return bfail(b, LE_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(ce));
   }

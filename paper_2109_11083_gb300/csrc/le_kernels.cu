@@ -6,7 +6,7 @@
 //   k_decide  dX(n+1) from the integer step (Eq. 4); rebuild trigger
 //             2*max|dr| + |shift of the sheared images since the build| >= skin;
 //             per-step slot-offset table; folds the previous step's samples
-//   [if rebuild: k_rb_bin -> radix sort -> k_rb_permute -> k_rb_ranges ->
+//   [if rebuild: k_rb_bin -> radix sort -> k_rb_permute (and cell ranges) ->
 //                k_rb_list -> k_rb_bonds -> k_rb_finish]
 //   k_force   LJ (Eq. 9/10) over the Verlet list + FENE (Eq. 11) under the LE
 //             minimum image; Ftot = Fc - xi m (v - v_s e_x) + random (Eq. 5);
@@ -1260,14 +1260,36 @@ __global__ void __launch_bounds__(256) k_import(Geom g, Dyn *__restrict__ d, Buf
   b.gid[i] = i;
 }
 
+// ----------------------------------------------------------- rebuild: ranges
+// cell_start[c] = first sorted slot of cell c (every entry written once).
+// Run inside the permute kernel after a sort; k_rb_ranges alone on restore.
+__device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__restrict__ skey,
+                                               int *__restrict__ cell_start, int bx) {
+  const int k = bx * blockDim.x + threadIdx.x;
+  if (k >= g.n) return;
+  const int c = min((int)skey[k], g.ncell - 1);
+  const int prev = k == 0 ? -1 : min((int)skey[k - 1], g.ncell - 1);
+  for (int cc = prev + 1; cc <= c; ++cc) cell_start[cc] = k;
+  if (k == g.n - 1)
+    for (int cc = c + 1; cc <= g.ncell; ++cc) cell_start[cc] = g.n;
+}
+__global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom g,
+                                                   const uint32_t *__restrict__ skey,
+                                                   int *__restrict__ cell_start) {
+  rb_ranges_body(g, skey, cell_start, (int)blockIdx.x);
+}
+
 // ---------------------------------------------------------- rebuild: permute
-// Gathers the re-based state into cell order.  Forces are not moved: the
-// pair kernel of the same step overwrites them before anything reads them.
+// Gathers the re-based state into cell order, and writes the cell ranges of
+// the same sorted slots (both read only the sorted keys).  Forces are not
+// moved: the pair kernel of the same step overwrites them before anything
+// reads them.
 template <class R>
 __device__ __forceinline__ void rb_permute_body(const Geom g, Dyn *__restrict__ d, Bufs<R> s0,
                                                 Bufs<R> s1, Work w,
                                                 const uint32_t *__restrict__ skey,
                                                 const uint32_t *__restrict__ sval, int bx) {
+  rb_ranges_body(g, skey, w.cell_start, bx);
   const int cur = d->cur;
   const Bufs<R> src = pick(cur, s0, s1);
   const Bufs<R> dst = with_cur_q(pick(1 - cur, s0, s1), d->qpar);
@@ -1312,24 +1334,6 @@ __global__ void __launch_bounds__(256) k_rb_permute(const __grid_constant__ Geom
                                                     Work w, const uint32_t *__restrict__ skey,
                                                     const uint32_t *__restrict__ sval) {
   rb_permute_body<R>(g, d, s0, s1, w, skey, sval, (int)blockIdx.x);
-}
-
-// ----------------------------------------------------------- rebuild: ranges
-// cell_start[c] = first sorted slot of cell c (every entry written once).
-__device__ __forceinline__ void rb_ranges_body(const Geom g, const uint32_t *__restrict__ skey,
-                                               int *__restrict__ cell_start, int bx) {
-  const int k = bx * blockDim.x + threadIdx.x;
-  if (k >= g.n) return;
-  const int c = min((int)skey[k], g.ncell - 1);
-  const int prev = k == 0 ? -1 : min((int)skey[k - 1], g.ncell - 1);
-  for (int cc = prev + 1; cc <= c; ++cc) cell_start[cc] = k;
-  if (k == g.n - 1)
-    for (int cc = c + 1; cc <= g.ncell; ++cc) cell_start[cc] = g.n;
-}
-__global__ void __launch_bounds__(256) k_rb_ranges(const __grid_constant__ Geom g,
-                                                   const uint32_t *__restrict__ skey,
-                                                   int *__restrict__ cell_start) {
-  rb_ranges_body(g, skey, cell_start, (int)blockIdx.x);
 }
 
 // Restore path (checkpoint or rollback): sort keys, build-time FP64
@@ -1748,12 +1752,17 @@ __global__ void __launch_bounds__(128) k_observe(Geom g, Dyn *__restrict__ d, Bu
 // ------------------------------------------------------------ batched steps
 // One launch per kernel kind for a whole batch group: each block locates its
 // member in the kind's block prefix table and runs that member's own kernel
-// body; the rebuild kinds exit for members whose step does not rebuild.
+// body.  The rebuild kinds look up the same in the kind's table of rebuilding
+// members (kb_activate), so their blocks past those members' exit at once.
 #define LE_MEMBER(KIND)                                            \
   const int *off_ = off + (KIND) * (M + 1);                        \
   const int m_ = batch_member(off_, M, (int)blockIdx.x);           \
   const MemberDev<R> &q = mem[m_];                                 \
   const int bx_ = (int)blockIdx.x - off_[m_]
+#define LE_ACTIVE(KIND)                                                                    \
+  int m_, bx_;                                                                             \
+  if (!batch_active(act + (KIND) * batch_act_stride(M), M, (int)blockIdx.x, m_, bx_)) return; \
+  const MemberDev<R> &q = mem[m_]
 
 template <class R>
 __global__ void __launch_bounds__(kDriftThreads) kb_drift(const MemberDev<R> *__restrict__ mem,
@@ -1768,51 +1777,119 @@ __global__ void __launch_bounds__(128) kb_decide(const MemberDev<R> *__restrict_
   decide_body(q.g, q.d, q.w, cudaGraphConditionalHandle(0), 0, 0);
 }
 
+// The rebuild tables of every kind (batch_act_stride) from the decisions
+// kb_decide has just written: per kind, a block-wide scan over the members
+// (in chunks of the block) of "rebuilds and has blocks of this kind" and of
+// the block counts of those that do.
+template <class R>
+__global__ void __launch_bounds__(kActThreads) kb_activate(const MemberDev<R> *__restrict__ mem,
+                                                           const int *__restrict__ off, int M,
+                                                           int *__restrict__ act) {
+  __shared__ int s_a[kBKinds][kActThreads / 32], s_b[kBKinds][kActThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = kActThreads / 32;
+  int ca[kBKinds], cb[kBKinds];  // members and blocks listed so far (the same in every thread)
+#pragma unroll
+  for (int k = 0; k < kBKinds; ++k) ca[k] = cb[k] = 0;
+  for (int m0 = 0; m0 < M; m0 += kActThreads) {
+    const int m = m0 + t;
+    const bool reb = m < M && mem[m].d->rebuild != 0;
+    int nb[kBKinds], ia[kBKinds], ib[kBKinds];
+#pragma unroll
+    for (int k = 0; k < kBKinds; ++k) {
+      const int *o = off + k * (M + 1);
+      nb[k] = reb ? o[m + 1] - o[m] : 0;
+      ia[k] = nb[k] > 0 ? 1 : 0;
+      ib[k] = nb[k];
+    }
+    // inclusive scans within the warp, then across the warps' totals
+#pragma unroll
+    for (int sh = 1; sh < 32; sh <<= 1) {
+#pragma unroll
+      for (int k = 0; k < kBKinds; ++k) {
+        const int xa = __shfl_up_sync(0xffffffffu, ia[k], sh);
+        const int xb = __shfl_up_sync(0xffffffffu, ib[k], sh);
+        if (lane >= sh) {
+          ia[k] += xa;
+          ib[k] += xb;
+        }
+      }
+    }
+    if (lane == 31) {
+#pragma unroll
+      for (int k = 0; k < kBKinds; ++k) {
+        s_a[k][warp] = ia[k];
+        s_b[k][warp] = ib[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBKinds; ++k) {
+      int pa = 0, pb = 0, ta = 0, tb = 0;
+      for (int w2 = 0; w2 < nw; ++w2) {
+        const int xa = s_a[k][w2], xb = s_b[k][w2];
+        if (w2 < warp) {
+          pa += xa;
+          pb += xb;
+        }
+        ta += xa;
+        tb += xb;
+      }
+      if (nb[k] > 0) {
+        int *a = act + k * batch_act_stride(M);
+        const int pos = ca[k] + pa + ia[k] - 1;
+        a[1 + pos] = m;
+        a[1 + M + pos] = cb[k] + pb + ib[k] - nb[k];
+      }
+      ca[k] += ta;
+      cb[k] += tb;
+    }
+    __syncthreads();  // the warp totals of the next chunk
+  }
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < kBKinds; ++k) {
+      int *a = act + k * batch_act_stride(M);
+      a[0] = ca[k];
+      a[1 + M + ca[k]] = cb[k];
+    }
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) kb_rb_bin(const MemberDev<R> *__restrict__ mem,
-                                                 const int *__restrict__ off, int M) {
-  LE_MEMBER(kB256);
-  if (!q.d->rebuild) return;
+                                                 const int *__restrict__ act, int M) {
+  LE_ACTIVE(kB256);
   rb_bin_body<R>(q.g, q.d, q.s0, q.s1, q.w, bx_);
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_rb_permute(const MemberDev<R> *__restrict__ mem,
-                                                     const int *__restrict__ off, int M) {
-  LE_MEMBER(kB256);
-  if (!q.d->rebuild) return;
+                                                     const int *__restrict__ act, int M) {
+  LE_ACTIVE(kB256);
   const int fin = q.sort_passes & 1;
   rb_permute_body<R>(q.g, q.d, q.s0, q.s1, q.w, q.w.key[fin], q.w.val[fin], bx_);
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) kb_rb_ranges(const MemberDev<R> *__restrict__ mem,
-                                                    const int *__restrict__ off, int M) {
-  LE_MEMBER(kB256);
-  if (!q.d->rebuild) return;
-  rb_ranges_body(q.g, q.w.key[q.sort_passes & 1], q.w.cell_start, bx_);
-}
-
-template <class R>
 __global__ void __launch_bounds__(kListMaxThreads, 3) kb_rb_list(
-    const MemberDev<R> *__restrict__ mem, const int *__restrict__ off, int M) {
-  LE_MEMBER(kBList);
-  if (!q.d->rebuild) return;
+    const MemberDev<R> *__restrict__ mem, const int *__restrict__ act, int M) {
+  LE_ACTIVE(kBList);
   rb_list_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, VBlock{bx_});
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) kb_rb_bonds(const MemberDev<R> *__restrict__ mem,
-                                                   const int *__restrict__ off, int M) {
-  LE_MEMBER(kB256);
-  if (!q.d->rebuild || q.g.maxb == 0) return;
+                                                   const int *__restrict__ act, int M) {
+  LE_ACTIVE(kB256);
+  if (q.g.maxb == 0) return;
   rb_bonds_body<R>(q.g, q.d, q.s0, q.s1, q.w, 0, bx_);
 }
 
 template <class R>
-__global__ void kb_rb_finish(const MemberDev<R> *__restrict__ mem) {
-  const MemberDev<R> &q = mem[blockIdx.x];
-  if (!q.d->rebuild) return;
+__global__ void kb_rb_finish(const MemberDev<R> *__restrict__ mem, const int *__restrict__ act,
+                             int M) {
+  LE_ACTIVE(kBOne);
+  (void)bx_;
   rb_finish_body(q.d, 0);
 }
 
@@ -1830,22 +1907,24 @@ __global__ void __launch_bounds__(256) kb_vcopy(const MemberDev<R> *__restrict__
   vcopy_body<R>(q.g, q.d, q.s0, q.s1, q.w, bx_);
 }
 #undef LE_MEMBER
+#undef LE_ACTIVE
 
 template <class R>
 void batch_step(const BatchGrid &bg, cudaStream_t st, bool drift, int mode) {
   const MemberDev<R> *mem = static_cast<const MemberDev<R> *>(bg.mem);
   const int M = bg.M;
   const int *off = bg.off;
+  const int *act = bg.act;
   const int n256 = bg.blocks[kB256];
   if (drift) kb_drift<R><<<n256, kDriftThreads, 0, st>>>(mem, off, M);
   kb_decide<R><<<M, 128, 0, st>>>(mem);
-  kb_rb_bin<R><<<n256, 256, 0, st>>>(mem, off, M);
+  kb_activate<R><<<1, kActThreads, 0, st>>>(mem, off, M, bg.act);
+  kb_rb_bin<R><<<n256, 256, 0, st>>>(mem, act, M);
   launch_batch_sort(bg, st);
-  kb_rb_permute<R><<<n256, 256, 0, st>>>(mem, off, M);
-  kb_rb_ranges<R><<<n256, 256, 0, st>>>(mem, off, M);
-  kb_rb_list<R><<<bg.blocks[kBList], bg.list_threads, 0, st>>>(mem, off, M);
-  if (bg.bonds) kb_rb_bonds<R><<<n256, 256, 0, st>>>(mem, off, M);
-  kb_rb_finish<R><<<M, 1, 0, st>>>(mem);
+  kb_rb_permute<R><<<n256, 256, 0, st>>>(mem, act, M);
+  kb_rb_list<R><<<bg.blocks[kBList], bg.list_threads, 0, st>>>(mem, act, M);
+  if (bg.bonds) kb_rb_bonds<R><<<n256, 256, 0, st>>>(mem, act, M);
+  kb_rb_finish<R><<<M, 1, 0, st>>>(mem, act, M);
   const size_t smem = sizeof(long long) * 3 * (size_t)bg.nbins;
   const int nf = bg.blocks[kBForce];
   if (bg.dpd) {
@@ -1936,7 +2015,6 @@ static void rebuild_tail(const SysDev &s, cudaStream_t st) {
 #define FN(R, A, B) k_rb_permute<R><<<nb, 256, 0, st>>>(s.g, s.dyn, A, B, s.w, skey, sval)
   LE_DISPATCH(s, FN);
 #undef FN
-  k_rb_ranges<<<nb, 256, 0, st>>>(s.g, skey, s.w.cell_start);
   const int nl = blocks_for(n, s.list_threads);
 #define FN(R, A, B) k_rb_list<R><<<nl, s.list_threads, 0, st>>>(s.g, s.dyn, A, B, s.w, 0)
   LE_DISPATCH(s, FN);

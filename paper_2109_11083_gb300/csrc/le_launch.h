@@ -101,16 +101,23 @@ __host__ __device__ inline void sort_pass_digit(int bits, int passes, int p, int
 }
 // Blocks of the count-table scan of pass p (0 when the sort has no pass p).
 int sort_scan_blocks(int bits, int blocks, int p);
+// Whether the count table of pass p is scanned by the three-kernel scan
+// (chunk sums, top level, apply) rather than in one block.
+bool sort_scan_large(int bits, int blocks, int p);
 
 // ------------------------------------------------------------ batched steps
 // A batch of independent systems advances with ONE launch per kernel kind:
 // every block finds its system in a per-kind prefix table of block counts
 // and runs that system's own kernel body on its own data, so each member's
 // trajectory is bit-identical to stepping it alone.  The rebuild kernels run
-// every step for every member; blocks of a member whose step decided "no
-// rebuild" exit at once.  Members of one launch share precision, bonds,
-// thermostat kind and launch shapes (a group).
+// every step with grids sized for every member; after the step decision a
+// one-block kernel lists, per kind, the members that rebuild and the prefix
+// of their block counts, so the first blocks of each rebuild launch are
+// exactly the rebuilding members' blocks and the rest exit after one load.
+// Members of one launch share precision, bonds, thermostat kind and launch
+// shapes (a group).
 constexpr int kMaxSortPasses = 4;
+constexpr int kActThreads = 256;  // block of kb_activate (members scanned per chunk)
 enum BatchKind : int {
   kB256 = 0,   // blocks_for(n, 256): drift, bin, permute, ranges, bonds, vcopy
   kBForce,     // blocks_for(n, force_threads)
@@ -131,10 +138,15 @@ template <class R> struct MemberDev {
 struct BatchGrid {
   const void *mem = nullptr;  // MemberDev<R>[M] in device memory
   const int *off = nullptr;   // [kBKinds][M + 1] block prefix per kind, device memory
+  int *act = nullptr;         // [kBKinds][batch_act_stride(M)] rebuilding members, device memory
   int M = 0;
   int blocks[kBKinds] = {};   // grid size per kind
   int prec = 1, bonds = 0, dpd = 0;
   int force_threads = 256, list_threads = 128, nbins = 1, passes = 1;
+  // pass p has a member whose count table needs the three-kernel scan
+  // (sort_scan_large); without one, the chunk-sum and top-level launches of
+  // that pass are left out (every table is scanned in one block)
+  bool scan_large[kMaxSortPasses] = {};
 };
 // One step of every member of the group (drift, decide, gated rebuild,
 // force).  drift = false skips the drift launch (the previous step's force
@@ -152,6 +164,22 @@ __device__ __forceinline__ int batch_member(const int *off, int M, int bid) {
     else hi = mid - 1;
   }
   return lo;
+}
+
+// Rebuild table of one kind: act[0] = A, the members that rebuild this step
+// (and have blocks of that kind); act[1 + a] = the a-th of them (in member
+// order); act[1 + M + a] = its first block, act[1 + M + A] = their total.
+__host__ __device__ constexpr int batch_act_stride(int M) { return 2 * M + 2; }
+// Member m and its own block index of block bid of a rebuild launch; false
+// for a block past the rebuilding members' blocks.
+__device__ __forceinline__ bool batch_active(const int *act, int M, int bid, int &m, int &bx) {
+  const int na = act[0];
+  const int *aoff = act + 1 + M;
+  if (bid >= aoff[na]) return false;  // also every block when na = 0 (aoff[0] = 0)
+  const int a = batch_member(aoff, na, bid);
+  m = act[1 + a];
+  bx = bid - aoff[a];
+  return true;
 }
 
 }  // namespace le

@@ -236,37 +236,42 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
 
 
 // ------------------------------------------------------------ batched sort
-// The same pass kernels for every member of a batch group in one launch;
-// blocks of members that do not rebuild this step (or have no pass p) exit.
+// The same pass kernels for every member of a batch group in one launch.
+// Each block finds its member in the kind's table of members that rebuild
+// this step (act: one kind's slice, batch_active); blocks past them, and
+// those of members with no pass p, exit.
 template <class R>
 __global__ void __launch_bounds__(kSortThreads) kb_rs_hist(const MemberDev<R> *__restrict__ mem,
-                                                           const int *__restrict__ off, int M, int p) {
-  const int m = batch_member(off, M, blockIdx.x);
+                                                           const int *__restrict__ act, int M, int p) {
+  int m, bx;
+  if (!batch_active(act, M, (int)blockIdx.x, m, bx)) return;
   const MemberDev<R> &q = mem[m];
-  if (!q.d->rebuild || p >= q.sort_passes) return;
+  if (p >= q.sort_passes) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
-  rs_hist_body(q.w.key[p & 1], q.g.n, shift, w, q.sort_blocks, q.w.hist, (int)blockIdx.x - off[m]);
+  rs_hist_body(q.w.key[p & 1], q.g.n, shift, w, q.sort_blocks, q.w.hist, bx);
 }
 
 template <class R>
 __global__ void __launch_bounds__(kScanThreads) kb_scan_sums(const MemberDev<R> *__restrict__ mem,
-                                                             const int *__restrict__ off, int M, int p) {
-  const int m = batch_member(off, M, blockIdx.x);
+                                                             const int *__restrict__ act, int M, int p) {
+  int m, bx;
+  if (!batch_active(act, M, (int)blockIdx.x, m, bx)) return;
   const MemberDev<R> &q = mem[m];
-  if (!q.d->rebuild) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
   const int mm = (1 << w) * q.sort_blocks;
   if (mm <= kScanSeqChunks * kScanChunk) return;  // a small table: scan_apply's first block
-  scan_sums_body(q.w.hist, mm, q.sort_part, (int)blockIdx.x - off[m]);
+  scan_sums_body(q.w.hist, mm, q.sort_part, bx);
 }
 
 template <class R>
 __global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *__restrict__ mem,
-                                                            int p) {
-  const MemberDev<R> &q = mem[blockIdx.x];
-  if (!q.d->rebuild || p >= q.sort_passes) return;
+                                                            const int *__restrict__ act, int M, int p) {
+  int m, bx;
+  if (!batch_active(act, M, (int)blockIdx.x, m, bx)) return;
+  const MemberDev<R> &q = mem[m];
+  if (p >= q.sort_passes) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
   const int mm = (1 << w) * q.sort_blocks;
@@ -276,14 +281,13 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_top(const MemberDev<R> *
 
 template <class R>
 __global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const MemberDev<R> *__restrict__ mem,
-                                                              const int *__restrict__ off, int M, int p) {
-  const int m = batch_member(off, M, blockIdx.x);
+                                                              const int *__restrict__ act, int M, int p) {
+  int m, bx;
+  if (!batch_active(act, M, (int)blockIdx.x, m, bx)) return;
   const MemberDev<R> &q = mem[m];
-  if (!q.d->rebuild) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
   const int mm = (1 << w) * q.sort_blocks;
-  const int bx = (int)blockIdx.x - off[m];
   if (mm <= kScanSeqChunks * kScanChunk) {
     if (bx == 0) scan_seq_body(q.w.hist, mm);  // the member's whole table
     return;
@@ -293,31 +297,34 @@ __global__ void __launch_bounds__(kScanThreads) kb_scan_apply(const MemberDev<R>
 
 template <class R>
 __global__ void __launch_bounds__(kSortThreads) kb_rs_scatter(const MemberDev<R> *__restrict__ mem,
-                                                              const int *__restrict__ off, int M, int p) {
-  const int m = batch_member(off, M, blockIdx.x);
+                                                              const int *__restrict__ act, int M, int p) {
+  int m, bx;
+  if (!batch_active(act, M, (int)blockIdx.x, m, bx)) return;
   const MemberDev<R> &q = mem[m];
-  if (!q.d->rebuild || p >= q.sort_passes) return;
+  if (p >= q.sort_passes) return;
   int shift, w;
   sort_pass_digit(q.g.sort_bits, q.sort_passes, p, shift, w);
   const int in = p & 1, out = in ^ 1;
   rs_scatter_body(q.w.key[in], q.w.val[in], q.w.key[out], q.w.val[out], q.g.n, shift, w,
-                  q.sort_blocks, q.w.hist, (int)blockIdx.x - off[m]);
+                  q.sort_blocks, q.w.hist, bx);
 }
 
 template <class R>
 void batch_sort_passes(const BatchGrid &bg, cudaStream_t st) {
   const MemberDev<R> *mem = static_cast<const MemberDev<R> *>(bg.mem);
-  const int M = bg.M, M1 = bg.M + 1;
-  const int *off_sort = bg.off + kBSort * M1;
+  const int M = bg.M, S = batch_act_stride(bg.M);
+  const int *act_sort = bg.act + kBSort * S, *act_one = bg.act + kBOne * S;
   for (int p = 0; p < bg.passes; ++p) {
-    const int *off_scan = bg.off + (kBScan0 + p) * M1;
+    const int *act_scan = bg.act + (kBScan0 + p) * S;
     const int nscan = bg.blocks[kBScan0 + p];
     if (nscan == 0) continue;
-    kb_rs_hist<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, off_sort, M, p);
-    kb_scan_sums<R><<<nscan, kScanThreads, 0, st>>>(mem, off_scan, M, p);
-    kb_scan_top<R><<<M, kScanThreads, 0, st>>>(mem, p);
-    kb_scan_apply<R><<<nscan, kScanThreads, 0, st>>>(mem, off_scan, M, p);
-    kb_rs_scatter<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, off_sort, M, p);
+    kb_rs_hist<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, act_sort, M, p);
+    if (bg.scan_large[p]) {
+      kb_scan_sums<R><<<nscan, kScanThreads, 0, st>>>(mem, act_scan, M, p);
+      kb_scan_top<R><<<M, kScanThreads, 0, st>>>(mem, act_one, M, p);
+    }
+    kb_scan_apply<R><<<nscan, kScanThreads, 0, st>>>(mem, act_scan, M, p);
+    kb_rs_scatter<R><<<bg.blocks[kBSort], kSortThreads, 0, st>>>(mem, act_sort, M, p);
   }
 }
 
@@ -346,6 +353,14 @@ int sort_scan_blocks(int bits, int blocks, int p) {
   sort_pass_digit(bits, passes, p, shift, w);
   const int m = (1 << w) * blocks;
   return (m + kScanChunk - 1) / kScanChunk;
+}
+
+bool sort_scan_large(int bits, int blocks, int p) {
+  const int passes = sort_passes_for(bits);
+  if (p >= passes) return false;
+  int shift, w;
+  sort_pass_digit(bits, passes, p, shift, w);
+  return (1 << w) * blocks > kScanSeqChunks * kScanChunk;
 }
 
 void radix_sort_pairs(uint32_t *key[2], uint32_t *val[2], uint32_t *hist, uint32_t *part, int n,

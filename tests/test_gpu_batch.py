@@ -145,6 +145,33 @@ def test_members_with_one_and_two_sort_passes_equal_alone_bitwise():
         s.close()
 
 
+def test_member_with_a_multi_block_count_table_scan_equal_alone_bitwise():
+    """A member large enough that its radix passes scan their count tables
+    with the three-kernel scan (1.1M particles: 39^3 cells, two passes of
+    8 bits, 256 buckets x 269 tiles of 4096 keys > 8 chunks of 4096), batched
+    with two small boxes whose tables are scanned in one block."""
+    specs = [{"n": 1_100_000, "rho": 0.8442, "shear_rate": 0.5, "seed": 510},
+             {"n": 900, "rho": 0.8, "shear_rate": 0.7, "seed": 511},
+             {"n": 5000, "rho": 0.75, "shear_rate": 0.02, "seed": 512}]
+    alone = [_box(s, 1) for s in specs]
+    mixed = [_box(s, 1) for s in specs]
+    c = alone[0].counters()
+    assert c["cells"][0] * c["cells"][1] * c["cells"][2] > 2 ** 15
+    for a in alone:
+        a.step(24)
+    with le.Batch() as b:
+        for m in mixed:
+            b.add(m)
+        b.step(24)
+    for a, m in zip(alone, mixed):
+        ra, va = a.positions()
+        rm, vm = m.positions()
+        assert np.array_equal(ra, rm) and np.array_equal(va, vm)
+        assert a.counters()["rebuilds"] == m.counters()["rebuilds"] > 1
+    for s in alone + mixed:
+        s.close()
+
+
 def test_a_member_error_rolls_every_member_back():
     """One member breaks a FENE bond (two bonded beads flying apart): the batch
     call reports it and every member is back at its state before the call."""
