@@ -399,9 +399,9 @@ def run_ours(args):
     # per step: decide, force, and a drift launch in the first step only (the
     # force launch of every other step ran its drift: FP32 without DPD); per
     # rebuild: bin, 5 per sort pass (counts, 3 scan kernels, scatter),
-    # permute, ranges, list, finish
+    # permute (with the cell ranges), list, finish
     fused = True  # this box runs FP32 with the Langevin thermostat
-    launches = (2 * args.steps + 1 if fused else 3 * args.steps) + rebuilds * (1 + 5 * passes + 4)
+    launches = (2 * args.steps + 1 if fused else 3 * args.steps) + rebuilds * (1 + 5 * passes + 3)
     mean_nb = c1["list_mean"]
     kbytes = force_kernel_bytes(w.n, mean_nb)
     f_avg_s = force_ms / args.steps * 1e-3
