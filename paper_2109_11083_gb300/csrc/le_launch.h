@@ -113,13 +113,13 @@ bool sort_scan_large(int bits, int blocks, int p);
 // every step with grids sized for every member; after the step decision a
 // one-block kernel lists, per kind, the members that rebuild and the prefix
 // of their block counts, so the first blocks of each rebuild launch are
-// exactly the rebuilding members' blocks and the rest exit after one load.
+// exactly the rebuilding members' blocks and the rest exit after two loads.
 // Members of one launch share precision, bonds, thermostat kind and launch
 // shapes (a group).
 constexpr int kMaxSortPasses = 4;
 constexpr int kActThreads = 256;  // block of kb_activate (members scanned per chunk)
 enum BatchKind : int {
-  kB256 = 0,   // blocks_for(n, 256): drift, bin, permute, ranges, bonds, vcopy
+  kB256 = 0,   // blocks_for(n, 256): drift, bin, permute (with the ranges), bonds, vcopy
   kBForce,     // blocks_for(n, force_threads)
   kBList,      // blocks_for(n, list_threads)
   kBSort,      // sort tiles
