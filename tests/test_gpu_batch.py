@@ -172,6 +172,29 @@ def test_member_with_a_multi_block_count_table_scan_equal_alone_bitwise():
         s.close()
 
 
+def test_batch_of_more_members_than_one_activation_chunk_equal_alone_bitwise():
+    """300 small members: the per-step table of rebuilding members is built
+    in chunks of 256 members (a running carry across chunks); sampled
+    members, including ones past the first chunk, equal the same box alone."""
+    specs = synth.batched_systems(count=300, nmin=500, nmax=900, seed=91)
+    mixed = [_box(s, 1, bins=4) for s in specs]
+    sample = list(range(0, 300, 23)) + [255, 256, 257, 299]
+    alone = {k: _box(specs[k], 1, bins=4) for k in sample}
+    for a in alone.values():
+        a.step(30)
+    with le.Batch() as b:
+        for m in mixed:
+            b.add(m)
+        b.step(30)
+    for k, a in alone.items():
+        ra, va = a.positions()
+        rm, vm = mixed[k].positions()
+        assert np.array_equal(ra, rm) and np.array_equal(va, vm), k
+        assert a.counters()["rebuilds"] == mixed[k].counters()["rebuilds"] > 1
+    for s in list(alone.values()) + mixed:
+        s.close()
+
+
 def test_a_member_error_rolls_every_member_back():
     """One member breaks a FENE bond (two bonded beads flying apart): the batch
     call reports it and every member is back at its state before the call."""
