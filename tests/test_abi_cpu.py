@@ -4,6 +4,7 @@ device work."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -52,6 +53,27 @@ def test_argument_checks_reject_bad_boxes_without_a_gpu(lib):
     p.profile_bins = 0
     with pytest.raises(lib.LEError) as e:
         lib.le_create([10.0, 10.0, 10.0], 0.1, 2.5, 0.3, p)
+    assert e.value.status == 1
+
+
+def test_degenerate_sizes_are_refused_on_the_host(lib):
+    """No particles, more than the 2^24 that a list entry can index, and a sort
+    key wider than its stated bit count are argument errors, found before any
+    device work; the largest indexable system is accepted."""
+    p = lib.le_default_params()
+    box = [20.0, 20.0, 20.0]
+    for n in (0, -5, (1 << 24) + 1):
+        with pytest.raises(lib.LEError) as e:
+            lib.le_estimate_device_bytes(box, 0.1, 2.5, 0.3, p, n)
+        assert e.value.status == 1
+    small = lib.le_estimate_device_bytes(box, 0.1, 2.5, 0.3, p, 1000)
+    largest = lib.le_estimate_device_bytes([270.0] * 3, 0.1, 2.5, 0.3, p, 1 << 24)
+    assert 0 < small < largest
+    with pytest.raises(lib.LEError) as e:
+        lib.le_sort_cell_keys(np.zeros(0, np.uint32), 8)
+    assert e.value.status == 1
+    with pytest.raises(lib.LEError) as e:
+        lib.le_sort_cell_keys(np.array([3, 300], np.uint32), 8)   # 300 needs 9 bits
     assert e.value.status == 1
 
 
